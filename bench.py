@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark: single-source SimRank queries/s at eps = 0.1 on a synthetic R-MAT graph.
+
+Workload (one GPU): R-MAT (a,b,c,d) = (.57,.19,.19,.05), n = 2^20, m = 2^24 distinct edges, seeded; query
+nodes drawn uniformly from the nodes with in-degree >= 1; c = 0.6, eps = 0.1, delta = 0.01 (n_r = 3,325),
+deterministic PROBE, FP32 scores.  A step is one single-source query through the C ABI (walks, tree,
+level loop, estimates), queries run one at a time; L2 is flushed between steps (outside the timed events).
+Also reported: the same queries in batches, the end-to-end number with host buffers, p50/p99 latency,
+the PROBE level kernel's achieved bandwidth against the measured HBM copy peak, and the CPU oracle on a
+bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle (the reference implementation of this build) on the same
+workload and metric.  Multi-GPU runs (torchrun) are replicas: each rank owns a copy of the graph and its
+own share of queries, with no collective on the data path.
+"""
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("single-source SimRank queries/sec @ε=0.1 (batched serving vs 1-at-a-time), p50/p99 ms, HBM GB/s")
+WORKLOAD = "rmat-20"
+EPS = 0.1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=8, help="queries per call in the batched leg")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001 -- file absent on some boxes
+        return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes / algorithmic bytes of the PROBE level kernel from the committed ncu summary, valid only
+    while the kernel source is unchanged since the capture (checked by its hash)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1709_06955_gb300", "csrc", "probe_level.cu")
+    summ = os.path.join(ROOT, "profiles", "k_pull_traffic.txt")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(summ):
+            if line.startswith("ratio "):
+                _, ratio, src_hash = line.split()[:3]
+                if src_hash == h:
+                    return float(ratio)
+    except Exception:  # noqa: BLE001
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:  # noqa: BLE001 -- no nvidia-smi
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out = self.proc.communicate(timeout=5)[0]
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(getattr(self, "out", ""))) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_workload(name):
+    from paper_1709_06955_gb300 import synth
+    n, s, d = synth.config_graph(name)
+    qs = synth.queries(n, d, 100, seed=2)
+    return n, s, d, qs
+
+
+def cpu_baseline(n, s, d, qs, budget_s):
+    """The oracle (Alg. 1, FP64, one thread) on walks 0, 1, 2, ... of query 0 until budget_s has passed;
+    queries/s extrapolated from the time per walk."""
+    from oracle import build as obuild, core
+    obuild.build()
+    O = core.Graph(n, s, d)
+    nr = core.num_walks(0.6, EPS, 0.01, n)
+    u = int(qs[0])
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        O.single_source(u, eps=EPS, seed=3, qid=0, walk_begin=k, walk_end=k + 1)
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or k >= 256:
+            break
+    per_walk = el / k
+    return {"value": 1.0 / (per_walk * nr), "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": "walks 0..%d of 1 query (of n_r=%d) on %s, Alg. 1 FP64 single-threaded, %.1f s; "
+                      "queries/s extrapolated from the time per walk" % (k - 1, nr, WORKLOAD, el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import build as obuild, core
+    obuild.build()
+    n, s, d, qs = load_workload(args.workload)
+    O = core.Graph(n, s, d)
+    nr = core.num_walks(0.6, EPS, 0.01, n)
+    # one step: one walk of one query through Alg. 1 (a bounded sample of the query)
+    for i in range(args.warmup):
+        O.single_source(int(qs[i % len(qs)]), eps=EPS, seed=3, qid=i, walk_begin=0, walk_end=1)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        q = i % len(qs)
+        O.single_source(int(qs[q]), eps=EPS, seed=3, qid=q, walk_begin=i // len(qs), walk_end=i // len(qs) + 1)
+    el = time.perf_counter() - t0
+    qps = args.steps / el / nr
+    line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "R-MAT (.57,.19,.19,.05) n=2^20 m=2^24, eps=0.1 delta=0.01 c=0.6",
+                       "step": "one walk of one query (Alg. 1 on it), queries/s = walks/s / n_r"},
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d walks over %d queries (of n_r=%d each)" % (args.steps, min(args.steps, len(qs)), nr)},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1709_06955_gb300 import build, probesim
+    build.build()
+    n, s, d, qs = load_workload(args.workload)
+    G = probesim.Graph(n, s, d)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    nq = len(qs)
+
+    def query(i):
+        j = rank * 100003 + i
+        return probesim.make_queries([qs[j % nq]], eps=EPS, k=50, query_ids=[j])
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
+    out = torch.zeros((1, n), dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up
+    for i in range(args.warmup):
+        G.single_source(query(i), out=out, stream=sptr)
+    torch.cuda.synchronize(dev)
+
+    # timed: K queries one at a time, device-resident output
+    G.set_profiling(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    agg = {"probe_ms": 0.0, "probe_bytes": 0.0, "probe_launches": 0, "kernel_launches": 0, "edge_gathers": 0,
+           "vectors": 0, "tree_nodes": 0, "walks": 0}
+    with ClockSampler(local) as clk:
+        barrier()
+        w0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            G.single_source(query(args.warmup + i), out=out, stream=sptr)
+            evs[i][1].record(stream)
+            st = G.stats()
+            for k in agg:
+                agg[k] += st[k]
+        barrier()
+        wall = time.perf_counter() - w0
+    G.set_profiling(False)
+    lat = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(lat)
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps / (tot_ms / 1e3)
+
+    # batched leg: the same number of queries, args.batch per call
+    B = max(1, args.batch)
+    nb = max(1, args.steps // B)
+    outb = torch.zeros((B, n), dtype=torch.float32, device=dev)
+    Qb = [probesim.make_queries([qs[(rank * 100003 + args.warmup + i * B + j) % nq] for j in range(B)], eps=EPS,
+                                query_ids=[rank * 100003 + args.warmup + i * B + j for j in range(B)])
+          for i in range(nb)]
+    G.single_source(Qb[0], out=outb, stream=sptr)
+    bev = []
+    barrier()
+    for i in range(nb):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.single_source(Qb[i], out=outb, stream=sptr)
+        b.record(stream)
+        bev.append((a, b))
+    barrier()
+    bms = sum(a.elapsed_time(b) for a, b in bev)
+    batched_qps = nb * B / (bms / 1e3)
+
+    # end-to-end through the C ABI with host buffers: query struct in, pinned host scores out
+    host_out = torch.empty((1, n), dtype=torch.float32, pin_memory=True)
+    e2e_steps = min(args.steps, 30)
+    barrier()
+    e0 = time.perf_counter()
+    for i in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        G.single_source(query(args.warmup + i), out=host_out, stream=sptr)
+    barrier()
+    e2e_s = time.perf_counter() - e0
+    e2e_qps = e2e_steps / e2e_s
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return 0
+
+    peak, peak_kind = measured_peak_hbm()
+    achieved = agg["probe_bytes"] / (agg["probe_ms"] / 1e3) / 1e9 if agg["probe_ms"] > 0 else None
+    ratio = recorded_traffic()
+    per_launch = agg["probe_bytes"] / max(1, agg["probe_launches"])
+    roof = {"kernel": "k_pull (PROBE level pull, probe_level.cu)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "peak_kind": peak_kind + " hbm_gbs (copy)", "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": (ratio * per_launch) if ratio else None,
+            "algorithmic_bytes_per_launch": per_launch, "launches": agg["probe_launches"],
+            "kernel_ms_share_of_step": agg["probe_ms"] / tot_ms if tot_ms else None,
+            "l2_gather_GBps": 4.0 * agg["edge_gathers"] / (agg["probe_ms"] / 1e3) / 1e9 if agg["probe_ms"] else None}
+    lat_sorted = sorted(lat)
+
+    def pct(p):
+        return lat_sorted[min(len(lat_sorted) - 1, int(round(p / 100.0 * (len(lat_sorted) - 1))))]
+
+    line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "R-MAT (.57,.19,.19,.05) n=2^20 m=2^24 seed 1, eps=0.1 delta=0.01 c=0.6 "
+                                   "(n_r=3325), deterministic PROBE, one query per call",
+                       "queries": "uniform over nodes with in-degree >= 1", "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "p50_ms": pct(50), "p99_ms": pct(99), "wall_s": wall,
+            "batched": {"batch": B, "value": batched_qps, "unit": "queries/s", "calls": nb},
+            "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": 32, "d2h_bytes_per_step": 4 * n,
+                    "steps": e2e_steps},
+            "roofline": roof, "clocks": clk.summary(), "gpu_launches": agg["kernel_launches"],
+            "work": {"walks_per_query": agg["walks"] / args.steps, "tree_nodes_per_query": agg["tree_nodes"] / args.steps,
+                     "vectors_per_query": agg["vectors"] / args.steps,
+                     "edge_gathers_per_query": agg["edge_gathers"] / args.steps}}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n, s, d, qs, args.cpu_seconds)
+    if world > 1:
+        torch.distributed.barrier()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

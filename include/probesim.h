@@ -1,0 +1,150 @@
+/*
+ * probesim.h -- C ABI of the GB300-native ProbeSim library (libprobesim.so).
+ *
+ * ProbeSim (Liu et al., "ProbeSim: Scalable Single-Source and Top-k SimRank Computations on Dynamic
+ * Graphs", PVLDB 11(1), 2017) answers approximate single-source SimRank queries (Def. 1) and top-k
+ * SimRank queries (Def. 2) on a directed simple graph without any index: n_r sqrt(c)-walks from the
+ * query node (Alg. 1), a PROBE from every walk prefix (Alg. 2, or Alg. 3 randomized), shared walk
+ * prefixes (Alg. 4) and the pruning rules of Sec. 4.1.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns a probesim_status; no exception or signal crosses the ABI.  On failure
+ *    probesim_last_error() returns a message for the calling thread.
+ *  - Node ids are int32 in [0, n).  An id outside that range makes the call fail with
+ *    PROBESIM_E_RANGE before anything is applied.
+ *  - The caller owns every input and output buffer.  Each one may be host memory or CUDA device memory;
+ *    the library tells them apart with cudaPointerGetAttributes.  Host buffers are read or written
+ *    before the call returns.  Device buffers are read or written on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream); the call synchronises `stream` before returning, so outputs are
+ *    complete on return either way.
+ *  - The library owns the graph and all scratch memory (device memory held by the graph object and
+ *    released by probesim_graph_destroy).
+ *  - A graph object may be used from several threads; calls on one graph are serialised internally.
+ *  - All arithmetic on the GPU is FP32 or integer; FP64 is used only on the host (n_r, thresholds).
+ */
+#ifndef PROBESIM_H
+#define PROBESIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct probesim_graph probesim_graph; /* opaque, owned by the library */
+
+typedef enum {
+    PROBESIM_OK = 0,
+    PROBESIM_E_INVALID = 1,     /* null pointer, size or parameter out of its documented range */
+    PROBESIM_E_RANGE = 2,       /* a node id outside [0, n) */
+    PROBESIM_E_NOMEM = 3,       /* a device or host allocation failed; the graph is unchanged */
+    PROBESIM_E_CUDA = 4,        /* a CUDA runtime error; the message names it */
+    PROBESIM_E_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    PROBESIM_E_BUSY = 6,        /* admission refused: not enough free slots or score-buffer memory */
+    PROBESIM_E_UNSUPPORTED = 7  /* a valid request this build does not implement */
+} probesim_status;
+
+/* PROBE variants (probesim_config.probe_mode). */
+enum {
+    PROBESIM_PROBE_DETERMINISTIC = 0, /* Alg. 2 */
+    PROBESIM_PROBE_RANDOMIZED = 1,    /* Alg. 3 */
+    PROBESIM_PROBE_SWITCH = 2         /* Sec. 4.4: deterministic, then randomized above c0 * w * n */
+};
+
+/* Graph-wide parameters, fixed at creation. */
+typedef struct {
+    double c;           /* SimRank decay factor of Eq. 1, 0 < c < 1 (the paper uses 0.6) */
+    double delta;       /* failure probability of Def. 1, 0 < delta < 1 */
+    int32_t l_max;      /* Pruning Rule 1 (Sec. 4.1): a walk keeps at most l_max nodes, 1 <= l_max <= 255 */
+    float eps_p;        /* Pruning Rule 2 (Sec. 4.1) threshold, >= 0; 0 disables the rule */
+    float c0;           /* switch constant of Sec. 4.4, >= 0 (used by PROBESIM_PROBE_SWITCH) */
+    int32_t probe_mode; /* PROBESIM_PROBE_* */
+    uint32_t seed;      /* first Philox key word of every walk and every randomized PROBE draw */
+} probesim_config;
+
+/* One query.  Its Philox key is (config.seed, query_id): walk k, step s draws counter (k, s, 0, 0), so a
+ * query's result does not depend on which other queries share its launch. */
+typedef struct {
+    int32_t node;       /* query node u */
+    int32_t k;          /* number of results for probesim_topk, 1 <= k <= n-1; ignored by single_source */
+    double eps;         /* sampling error of Alg. 1; n_r = ceil(3c/eps^2 * ln(n/delta)), 0 < eps < 1 */
+    uint32_t query_id;  /* second Philox key word */
+    int32_t walk_begin; /* use walks k in [walk_begin, walk_end) of the n_r walks (the estimate still */
+    int32_t walk_end;   /* divides by n_r); walk_end <= 0 means n_r.  0/0 is the full estimator */
+} probesim_query;
+
+/* Fills *cfg with c = 0.6, delta = 0.01, l_max = 64, eps_p = 0, c0 = 1, deterministic PROBE, seed = 3. */
+probesim_status probesim_config_default(probesim_config *cfg);
+
+/* Builds the device graph store from m directed edges src[e] -> dst[e] (Sec. 2.1: a directed simple
+ * graph).  Self-loops and duplicate edges are dropped (a simple graph has neither) and the number kept
+ * is reported by probesim_graph_info.  n >= 1, 0 <= m < 2^31.  On success *out owns the graph. */
+probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32_t *dst, int64_t m,
+                                      const probesim_config *cfg, void *stream, probesim_graph **out);
+
+/* Frees the graph and all its device memory.  NULL is accepted. */
+probesim_status probesim_graph_destroy(probesim_graph *g);
+
+/* Current node count, edge count, and update epoch (the number of update batches applied). */
+probesim_status probesim_graph_info(const probesim_graph *g, int32_t *n, int64_t *m, uint64_t *epoch);
+
+/* Dynamic updates (the paper's index-free design needs no rebuild, Sec. 1): apply k edge insertions or
+ * deletions as one batch that advances the epoch.  Inserting an existing edge, deleting an absent edge and
+ * self-loops are skipped; *applied (may be NULL) receives the number of edges actually changed.  Queries
+ * issued after the call returns see the new edge set. */
+probesim_status probesim_insert_edges(probesim_graph *g, const int32_t *src, const int32_t *dst, int64_t k,
+                                      int64_t *applied, void *stream);
+probesim_status probesim_delete_edges(probesim_graph *g, const int32_t *src, const int32_t *dst, int64_t k,
+                                      int64_t *applied, void *stream);
+
+/* n_r = ceil(3c/eps^2 * ln(n/delta)) for this graph (Alg. 1 line 1), computed in FP64 on the host. */
+probesim_status probesim_num_walks(const probesim_graph *g, double eps, int64_t *n_r);
+
+/* The sqrt(c)-walks of the queries (Def. 3, truncated by Pruning Rule 1), for checking.  Walks are laid out
+ * query by query, walk by walk (walk_begin..walk_end-1 of each): nodes[w * l_max + s] is node s+1 of walk w
+ * (entries past its length are -1) and lens[w] its node count.  capacity is the number of walk rows the
+ * buffers hold; PROBESIM_E_INVALID if the queries need more. */
+probesim_status probesim_sample_walks(probesim_graph *g, const probesim_query *q, int32_t nq, int32_t *nodes,
+                                      int32_t *lens, int64_t capacity, void *stream);
+
+/* Approximate single-source SimRank (Def. 1, Alg. 1 / Alg. 4): scores[i * n + v] = s~(q[i].node, v), with
+ * s~(u, u) = 1.  scores holds nq * n floats. */
+probesim_status probesim_single_source(probesim_graph *g, const probesim_query *q, int32_t nq, float *scores,
+                                       void *stream);
+
+/* Approximate top-k SimRank (Def. 2): for query i, ids[i * kmax + r] and vals[i * kmax + r], r < q[i].k, are
+ * the nodes v != u with the largest s~(u, v), ordered by (s~ descending, id ascending); entries r >= q[i].k
+ * are set to -1 and 0.  1 <= q[i].k <= kmax <= n-1. */
+probesim_status probesim_topk(probesim_graph *g, const probesim_query *q, int32_t nq, int32_t kmax, int32_t *ids,
+                              float *vals, void *stream);
+
+/* Per-call measurements of the last single_source/topk call on this graph.  When profiling is on, the
+ * library records CUDA events around every launch of the PROBE level kernel (the dominant kernel) on the
+ * call's stream; probe_ms is their summed duration and probe_launches their count.  probe_bytes is the
+ * algorithmic byte count of those launches (see the field comments).  Profiling adds event records but
+ * skips no work. */
+typedef struct {
+    int64_t walks;          /* walks generated */
+    int64_t walk_nodes;     /* sum of walk lengths */
+    int64_t tree_nodes;     /* reverse-reachability tree nodes (Alg. 4), the virtual super-roots included */
+    int64_t vectors;        /* dense score vectors pushed (tree nodes with a subtree of height >= 2) */
+    int64_t levels;         /* level-loop iterations */
+    int64_t edge_gathers;   /* (edge, vector) pairs processed by the PROBE level kernel */
+    int64_t probe_launches; /* launches of the PROBE level kernel */
+    double probe_ms;        /* their summed CUDA-event duration (profiling on), else 0 */
+    double probe_bytes;     /* algorithmic bytes of those launches: 4 per edge index and 4 per gathered
+                               score per vector-edge, 4 per written score, 12 per vertex per tile */
+    int64_t kernel_launches;/* all kernels this library launched in the call */
+} probesim_stats;
+
+probesim_status probesim_set_profiling(probesim_graph *g, int32_t on);
+probesim_status probesim_get_stats(const probesim_graph *g, probesim_stats *out);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *probesim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROBESIM_H */

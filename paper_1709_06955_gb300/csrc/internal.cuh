@@ -1,0 +1,145 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/probesim.h"
+
+namespace ps {
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As Easy as 1, 2, 3",
+// SC'11): ten rounds of two 32x32->64-bit multiplies over a 4-word counter, the key advanced by a
+// Weyl sequence between rounds.  Walk k, step s of a query keyed (seed, query_id) uses counter
+// (k, s, 0, 0); a randomized PROBE draw of walk k on prefix length i, level j, candidate x uses
+// counter (k, 2^24 | i << 8 | j, x, 0).
+// ---------------------------------------------------------------------------------------------
+struct U32x4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                               uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return U32x4{c0, c1, c2, c3};
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device graph store: in-adjacency I(v) sorted by source id (walks pick the k-th entry), out-
+// adjacency O(x) sorted by destination id, w[v] = sqrt(c)/|I(v)| (0 when |I(v)| = 0), and the work
+// decomposition of the pull kernel: every in-list cut into pieces of at most kPiece edges, ordered
+// by length (longest first).  A piece of a vertex cut into several pieces is added atomically.
+// ---------------------------------------------------------------------------------------------
+constexpr int kPiece = 64;
+
+struct DeviceGraph {
+    int32_t n = 0;
+    int64_t m = 0;
+    int64_t *in_off = nullptr;
+    int32_t *in_col = nullptr;
+    int64_t *out_off = nullptr;
+    int32_t *out_col = nullptr;
+    float *w = nullptr;
+    int64_t n_pieces = 0;
+    int32_t *piece_v = nullptr;
+    int64_t *piece_beg = nullptr;
+    int32_t *piece_len = nullptr;  // length | (split ? 1 << 31 : 0)
+    int32_t n_split = 0;           // vertices cut into more than one piece
+    int32_t *split_v = nullptr;
+};
+
+// The queries of one launch.
+struct QueryBatch {
+    int32_t B = 0;
+    const int32_t *node = nullptr;     // u per query
+    const uint32_t *qid = nullptr;     // Philox key word 1 per query
+    const int32_t *walk_base = nullptr;  // [B+1] prefix sums of walk counts
+    const int32_t *walk_k0 = nullptr;  // index of the first walk per query
+    const float *inv_nr = nullptr;     // 1/n_r per query (FP32)
+};
+
+// Reverse-reachability tree of Alg. 4 for all queries of a launch, stored as an open-addressing hash
+// table keyed by (parent slot, graph node); the slot index is the tree-node id.  Every query also has a
+// virtual super-root at depth 0 whose only child is the root u at depth 1.
+struct TrieTable {
+    int64_t cap = 0;           // power of two
+    unsigned long long *key = nullptr;
+    int32_t *node = nullptr;   // graph node (-1 for a super-root)
+    int32_t *parent = nullptr; // parent slot (-1 for a super-root)
+    int32_t *depth = nullptr;  // 0 super-root, 1 root, i for the prefix (u_1..u_i)
+    int32_t *query = nullptr;  // query index in the launch
+    int32_t *weight = nullptr; // walks sharing the prefix
+    int32_t *height = nullptr; // longest path below the node
+    int32_t *slot = nullptr;   // column of the node's score vector at its depth, -1 if it has none
+    float *gamma = nullptr;    // normalised weight minus the excluded score (see probe_level.cu)
+    float *G = nullptr;        // sum of the children's gamma
+};
+
+constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
+constexpr uint32_t kRhoTag = 0xFFFFFFFEu;
+
+// Device-side counters of one launch (read back with one small copy).
+struct LaunchCounters {
+    unsigned long long walk_nodes;
+    int32_t max_len;
+    int32_t overflow;  // hash table full
+};
+
+// ---------------------------------------------------------------------------------------------
+// Launchers (each launches one kernel on `s`).
+// ---------------------------------------------------------------------------------------------
+void launch_walks(const DeviceGraph &g, const QueryBatch &q, int32_t W, int32_t l_max, uint32_t t_stop,
+                  uint32_t seed, int32_t *walks, int32_t *lens, bool pad, LaunchCounters *ctr, cudaStream_t s);
+void launch_trie_insert(const DeviceGraph &g, const QueryBatch &q, int32_t W, int32_t l_max, const int32_t *walks,
+                        const int32_t *lens, TrieTable t, LaunchCounters *ctr, cudaStream_t s);
+void launch_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, cudaStream_t s);
+void launch_sched_lists(TrieTable t, const int32_t *node_off, const int32_t *slot_off, int32_t *ncur,
+                        int32_t *node_list, int32_t *slot_entry, int32_t *nchild, int32_t *rho_slot, cudaStream_t s);
+void launch_scan_exclusive(const int32_t *in, int32_t *out, int32_t count, cudaStream_t s);  // out has count+1
+void launch_sched_children(TrieTable t, const int32_t *slot_entry, int32_t S_total, const int32_t *slot_off,
+                           const int32_t *child_off, int32_t *ccur, int32_t *child_list, cudaStream_t s);
+
+void launch_dbuild(int32_t n, const float *MDp, int32_t pp, float *D, int32_t pd, int32_t S, const int32_t *child_off,
+                   const int32_t *child_list, cudaStream_t s);
+void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, int32_t pd, cudaStream_t s);
+void launch_zero_split_rows(const DeviceGraph &g, float *MD, int32_t pitch, cudaStream_t s);
+void launch_pull(const DeviceGraph &g, const float *D, float *MD, int32_t pitch, int32_t tile, cudaStream_t s);
+void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, const float *inv_nr,
+                  const float *MD, int32_t pc, cudaStream_t s);
+void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,
+                     int32_t p0, float *out, cudaStream_t s);
+
+// top-k: scores [B][n] on the device; ids/vals [B][kmax]
+struct TopkScratch {
+    unsigned int *hist = nullptr;     // [B][256]
+    unsigned int *state = nullptr;    // [B][4]: prefix, k_remaining, gt count cursor, tie base
+    unsigned int *tiecnt = nullptr;   // [B][blocks]
+    int32_t *cand_id = nullptr;       // [B][kmax]
+    float *cand_val = nullptr;        // [B][kmax]
+};
+int topk_blocks_per_query(int32_t n);
+void launch_topk(int32_t n, int32_t B, const float *scores, const int32_t *qnode, const int32_t *qk, int32_t kmax,
+                 TopkScratch sc, int32_t *ids, float *vals, cudaStream_t s, int64_t *launches);
+
+// pull tile width for a vector count
+int32_t pull_tile_for(int32_t S);
+inline int32_t round_up(int32_t x, int32_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace ps

@@ -1,0 +1,268 @@
+// PROBE level loop over the reverse-reachability tree (Alg. 2 / Alg. 4), regrouped.
+//
+// Alg. 4 probes every tree node r_q (the prefix (u_1..u_q)) with q-1 levels of Alg. 2 and adds
+// w_q/n_r * PROBE(u_1..u_q).  Writing one level of Alg. 2 as a linear map, Score_{j+1} = X_a M Score_j
+// with (M y)[v] = sqrt(c)/|I(v)| * sum_{x in I(v)} y[x] and X_a zeroing entry a = u_{q-j-1}, the sum over
+// all tree nodes factors along the tree (Horner's rule): for a tree node t with graph node a,
+//     C(t)  = sum over children s of Y(s),        Y(s) = w_s/n_r e_{a_s} + X_{a_s} M C(s),
+// and the estimate is M C(root) (entry u then set to 1).  Because X_a only removes entry a,
+//     X_a M C = M C - beta e_a,   beta = (M C)[a] = sqrt(c)/|I(a)| * sum_{x in I(a)} C[x],
+// so with gamma_s = w_s/n_r - beta_s the children of one tree node share one application of M:
+//     C(t) = M D(t) + sum_s gamma_s e_{a_s},  D(t) = sum over children s of C(s).
+// A tree node whose subtree has height >= 2 owns a dense score vector MD(t) = M D(t) (a "slot");
+// lower nodes only contribute their sparse gamma terms.  The level loop runs from the deepest depth to
+// the virtual super-root (depth 0, whose only child is the root u):
+//   dbuild   D(t)[x]  = sum of the children's MD columns                (segmented row sums)
+//   scatter  D(t)[a_g] += gamma_g for every grandchild g of t            (sparse terms)
+//   pull     MD(t)[v] = sqrt(c)/|I(v)| * sum_{x in I(v)} D(t)[x]         (the dominant kernel)
+//   gamma    gamma_t  = w_t/n_r - sqrt(c)/|I(a_t)| * (sum_{x in I(a_t)} MD(t)[x] + G_t),  G_parent += gamma_t
+// The result is exactly Alg. 4's (up to FP32 rounding); the work is one pull per slot instead of
+// q-1 pushes per tree node.  Score vectors of one depth are stored node-major, [n][pitch] FP32.
+#include "internal.cuh"
+
+namespace ps {
+
+// ------------------------------------------------------------------------------------------------
+// dbuild: one warp per row x; D[x][p] = sum_{c in children(p)} MDp[x][c], zero for padding columns.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_dbuild(int32_t n, const float *__restrict__ MDp, int32_t pp,
+                                                float *__restrict__ D, int32_t pd, int32_t S,
+                                                const int32_t *__restrict__ child_off,
+                                                const int32_t *__restrict__ child_list) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp; x < n; x += nwarps) {
+        const float *src = MDp + x * pp;
+        float *dst = D + x * pd;
+        for (int32_t p = lane; p < pd; p += 32) {
+            float acc = 0.f;
+            if (p < S) {
+                const int32_t cb = __ldg(child_off + p), ce = __ldg(child_off + p + 1);
+                for (int32_t c = cb; c < ce; ++c) acc += __ldg(src + __ldg(child_list + c));
+            }
+            dst[p] = acc;
+        }
+    }
+}
+
+static int grid_for(int64_t work, int threads, int per_sm) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+
+void launch_dbuild(int32_t n, const float *MDp, int32_t pp, float *D, int32_t pd, int32_t S, const int32_t *child_off,
+                   const int32_t *child_list, cudaStream_t s) {
+    const int blocks = grid_for((int64_t)n * 32, 256, 8);
+    k_dbuild<<<blocks, 256, 0, s>>>(n, MDp, pp, D, pd, S, child_off, child_list);
+}
+
+// ------------------------------------------------------------------------------------------------
+// scatter: for every tree node g at depth t+2, D[a_g][slot(grandparent(g))] += gamma_g.
+// ------------------------------------------------------------------------------------------------
+__global__ void k_scatter_gamma(const int32_t *__restrict__ nodes, int32_t cnt, TrieTable t, float *D, int32_t pd) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int32_t e = nodes[i];
+    const int32_t gp = t.parent[t.parent[e]];
+    atomicAdd(D + (int64_t)t.node[e] * pd + t.slot[gp], t.gamma[e]);
+}
+
+void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, int32_t pd, cudaStream_t s) {
+    if (cnt <= 0) return;
+    k_scatter_gamma<<<(cnt + 255) / 256, 256, 0, s>>>(nodes, cnt, t, D, pd);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Rows of vertices whose in-list is cut into several pieces receive atomic adds: zero them first.
+// ------------------------------------------------------------------------------------------------
+__global__ void k_zero_rows(const int32_t *__restrict__ rows, int32_t cnt, float *MD, int32_t pitch) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)cnt * pitch;
+    if (i >= total) return;
+    const int64_t r = i / pitch, c = i - r * pitch;
+    MD[(int64_t)rows[r] * pitch + c] = 0.f;
+}
+
+void launch_zero_split_rows(const DeviceGraph &g, float *MD, int32_t pitch, cudaStream_t s) {
+    const int64_t total = (int64_t)g.n_split * pitch;
+    if (total <= 0) return;
+    k_zero_rows<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g.split_v, g.n_split, MD, pitch);
+}
+
+// ------------------------------------------------------------------------------------------------
+// pull: MD[v][tile] = w[v] * sum_{x in I(v)} D[x][tile] over one tile of T columns (grid.y = tile).
+// A group of L = T/4 lanes (1 lane for T <= 2) owns one piece of an in-list and gathers VEC = min(T,4)
+// floats per lane per in-neighbour row; pieces are ordered longest first so the groups of a warp run
+// similar trip counts.  Column indices are loaded eight at a time and broadcast within the group, so
+// eight row gathers are in flight per lane.
+// ------------------------------------------------------------------------------------------------
+template <int VEC>
+struct VecT;
+template <>
+struct VecT<1> {
+    using type = float;
+    __device__ static float load(const float *p) { return __ldg(p); }
+};
+template <>
+struct VecT<2> {
+    using type = float2;
+    __device__ static float2 load(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+};
+template <>
+struct VecT<4> {
+    using type = float4;
+    __device__ static float4 load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+};
+
+__device__ __forceinline__ void vadd(float &a, float b) { a += b; }
+__device__ __forceinline__ void vadd(float2 &a, float2 b) { a.x += b.x; a.y += b.y; }
+__device__ __forceinline__ void vadd(float4 &a, float4 b) { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
+__device__ __forceinline__ float vscale(float a, float s) { return a * s; }
+__device__ __forceinline__ float2 vscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float4 vscale(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
+template <class V>
+__device__ __forceinline__ V vzero();
+template <>
+__device__ __forceinline__ float vzero<float>() { return 0.f; }
+template <>
+__device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+template <>
+__device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void vatomic(float *p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void vatomic(float *p, float2 v) { atomicAdd(reinterpret_cast<float2 *>(p), v); }
+__device__ __forceinline__ void vatomic(float *p, float4 v) { atomicAdd(reinterpret_cast<float4 *>(p), v); }
+__device__ __forceinline__ void vstore(float *p, float v) { *p = v; }
+__device__ __forceinline__ void vstore(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+__device__ __forceinline__ void vstore(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+template <int T>
+__global__ void __launch_bounds__(256) k_pull(const int32_t *__restrict__ piece_v, const int64_t *__restrict__ piece_beg,
+                                              const int32_t *__restrict__ piece_len, int64_t n_pieces,
+                                              const int32_t *__restrict__ in_col, const float *__restrict__ w,
+                                              const float *__restrict__ D, float *__restrict__ MD, int32_t pitch) {
+    constexpr int VEC = T >= 4 ? 4 : T;
+    constexpr int L = T / VEC;         // lanes per group
+    constexpr int CH = 8;              // in-neighbours per chunk
+    constexpr int PER = CH / L;        // column indices loaded per lane per chunk
+    using V = typename VecT<VEC>::type;
+    const int lane = threadIdx.x & 31;
+    const int lig = lane % L;
+    const unsigned gmask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (lane - lig));
+    const int32_t col0 = blockIdx.y * T + lig * VEC;
+    const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L;
+    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / L;
+    for (int64_t p = gid; p < n_pieces; p += ngroups) {
+        const int32_t v = __ldg(piece_v + p);
+        const int64_t beg = __ldg(piece_beg + p);
+        const int32_t info = __ldg(piece_len + p);
+        const int32_t len = info & 0x7fffffff;
+        V acc = vzero<V>();
+        for (int32_t e0 = 0; e0 < len; e0 += CH) {
+            int32_t mine[PER];
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int32_t e = e0 + lig + L * r;
+                mine[r] = e < len ? __ldg(in_col + beg + e) : -1;
+            }
+            V val[CH];
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                const int32_t x = L == 1 ? mine[j] : __shfl_sync(gmask, mine[j / L], j % L, L);
+                val[j] = x >= 0 ? VecT<VEC>::load(D + (int64_t)x * pitch + col0) : vzero<V>();
+            }
+#pragma unroll
+            for (int j = 0; j < CH; ++j) vadd(acc, val[j]);
+        }
+        const V res = vscale(acc, __ldg(w + v));
+        float *dst = MD + (int64_t)v * pitch + col0;
+        if (info < 0) vatomic(dst, res); else vstore(dst, res);
+    }
+}
+
+int32_t pull_tile_for(int32_t S) {
+    if (S <= 1) return 1;
+    if (S <= 2) return 2;
+    if (S <= 4) return 4;
+    if (S <= 8) return 8;
+    return 16;
+}
+
+void launch_pull(const DeviceGraph &g, const float *D, float *MD, int32_t pitch, int32_t tile, cudaStream_t s) {
+    const int32_t ntiles = pitch / tile;
+    const int L = tile >= 4 ? tile / 4 : 1;
+    const int64_t threads_needed = g.n_pieces * L;
+    const int blocks = grid_for(threads_needed, 256, 8);
+    dim3 grid(blocks, ntiles);
+    switch (tile) {
+        case 1: k_pull<1><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
+        case 2: k_pull<2><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
+        case 4: k_pull<4><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
+        case 8: k_pull<8><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
+        default: k_pull<16><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// gamma: one warp per tree node t at the current depth.
+//   beta_t  = sqrt(c)/|I(a_t)| * (sum_{x in I(a_t)} MD(t)[x] + G_t)   (the score PROBE would give a_t)
+//   gamma_t = w_t / n_r - beta_t;  G_parent += gamma_t
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gamma(const int64_t *__restrict__ in_off, const int32_t *__restrict__ in_col,
+                                               const float *__restrict__ w, const int32_t *__restrict__ nodes,
+                                               int32_t cnt, TrieTable t, const float *__restrict__ inv_nr,
+                                               const float *__restrict__ MD, int32_t pc) {
+    const int lane = threadIdx.x & 31;
+    const int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= cnt) return;
+    const int32_t e = nodes[i];
+    const int32_t a = t.node[e];
+    const int32_t sl = t.slot[e];
+    float sum = 0.f;
+    if (sl >= 0 && MD != nullptr) {
+        const int64_t beg = in_off[a], end = in_off[a + 1];
+        for (int64_t k = beg + lane; k < end; k += 32) sum += __ldg(MD + (int64_t)__ldg(in_col + k) * pc + sl);
+    }
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+        const float beta = __ldg(w + a) * (sum + t.G[e]);
+        const float g = (float)t.weight[e] * inv_nr[t.query[e]] - beta;
+        t.gamma[e] = g;
+        const int32_t p = t.parent[e];
+        if (p >= 0) atomicAdd(&t.G[p], g);
+    }
+}
+
+void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, const float *inv_nr,
+                  const float *MD, int32_t pc, cudaStream_t s) {
+    if (cnt <= 0) return;
+    const int64_t threads = (int64_t)cnt * 32;
+    k_gamma<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(g.in_off, g.in_col, g.w, nodes, cnt, t, inv_nr, MD, pc);
+}
+
+// ------------------------------------------------------------------------------------------------
+// finalize: out[q][v] = MD0[v][rho_slot(q)], out[q][u_q] = 1 (s(u,u) = 1).
+// ------------------------------------------------------------------------------------------------
+__global__ void k_finalize(int32_t n, int32_t B, const int32_t *__restrict__ qnode, const int32_t *__restrict__ rho_slot,
+                           const float *__restrict__ MD0, int32_t p0, float *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t q = blockIdx.y;
+    if (i >= n) return;
+    const int32_t sl = rho_slot[q];
+    float v = sl >= 0 ? MD0[i * p0 + sl] : 0.f;
+    if ((int32_t)i == qnode[q]) v = 1.f;
+    out[(int64_t)q * n + i] = v;
+}
+
+void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,
+                     int32_t p0, float *out, cudaStream_t s) {
+    dim3 grid((unsigned)((n + 255) / 256), (unsigned)B);
+    k_finalize<<<grid, 256, 0, s>>>(n, B, qnode, rho_slot, MD0, p0, out);
+}
+
+}  // namespace ps

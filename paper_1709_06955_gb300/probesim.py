@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libprobesim.so (include/probesim.h).
+
+Argument marshalling only: every step of a query runs in the library's CUDA kernels.  Buffers may be
+numpy arrays (host) or torch tensors (host or CUDA); device outputs are torch tensors on the current
+CUDA device.  ``load()`` raises if the library has not been built -- there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libprobesim.so")
+
+OK, E_INVALID, E_RANGE, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_UNSUPPORTED = range(8)
+PROBE_DETERMINISTIC, PROBE_RANDOMIZED, PROBE_SWITCH = 0, 1, 2
+
+EXPORTS = [
+    "probesim_config_default", "probesim_graph_create", "probesim_graph_destroy", "probesim_graph_info",
+    "probesim_insert_edges", "probesim_delete_edges", "probesim_num_walks", "probesim_sample_walks",
+    "probesim_single_source", "probesim_topk", "probesim_set_profiling", "probesim_get_stats",
+    "probesim_last_error",
+]
+
+
+class Config(C.Structure):
+    _fields_ = [("c", C.c_double), ("delta", C.c_double), ("l_max", C.c_int32), ("eps_p", C.c_float),
+                ("c0", C.c_float), ("probe_mode", C.c_int32), ("seed", C.c_uint32)]
+
+
+class Query(C.Structure):
+    _fields_ = [("node", C.c_int32), ("k", C.c_int32), ("eps", C.c_double), ("query_id", C.c_uint32),
+                ("walk_begin", C.c_int32), ("walk_end", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("walks", C.c_int64), ("walk_nodes", C.c_int64), ("tree_nodes", C.c_int64), ("vectors", C.c_int64),
+                ("levels", C.c_int64), ("edge_gathers", C.c_int64), ("probe_launches", C.c_int64),
+                ("probe_ms", C.c_double), ("probe_bytes", C.c_double), ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ProbeSimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("probesim status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path=None):
+    """Loads libprobesim.so (built by ``paper_1709_06955_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libprobesim.so is not built (%s); run paper_1709_06955_gb300.build.build()" % path)
+    L = C.CDLL(path)
+    P = C.POINTER
+    vp = C.c_void_p
+    L.probesim_last_error.restype = C.c_char_p
+    L.probesim_config_default.argtypes = [P(Config)]
+    L.probesim_graph_create.argtypes = [C.c_int32, vp, vp, C.c_int64, P(Config), vp, P(vp)]
+    L.probesim_graph_destroy.argtypes = [vp]
+    L.probesim_graph_info.argtypes = [vp, P(C.c_int32), P(C.c_int64), P(C.c_uint64)]
+    L.probesim_insert_edges.argtypes = [vp, vp, vp, C.c_int64, P(C.c_int64), vp]
+    L.probesim_delete_edges.argtypes = [vp, vp, vp, C.c_int64, P(C.c_int64), vp]
+    L.probesim_num_walks.argtypes = [vp, C.c_double, P(C.c_int64)]
+    L.probesim_sample_walks.argtypes = [vp, P(Query), C.c_int32, vp, vp, C.c_int64, vp]
+    L.probesim_single_source.argtypes = [vp, P(Query), C.c_int32, vp, vp]
+    L.probesim_topk.argtypes = [vp, P(Query), C.c_int32, C.c_int32, vp, vp, vp]
+    L.probesim_set_profiling.argtypes = [vp, C.c_int32]
+    L.probesim_get_stats.argtypes = [vp, P(Stats)]
+    for name in EXPORTS:
+        if name != "probesim_last_error":
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != OK:
+        raise ProbeSimError(st, load().probesim_last_error().decode())
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(x.ctypes.data)
+
+
+def _int32(x):
+    if _is_torch(x):
+        import torch
+        return x.to(torch.int32).contiguous()
+    return np.ascontiguousarray(x, dtype=np.int32)
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # noqa: BLE001 -- a missing torch only means the default stream
+        pass
+    return C.c_void_p(0)
+
+
+def default_config(**kw):
+    cfg = Config()
+    _check(load().probesim_config_default(C.byref(cfg)))
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def make_queries(nodes, eps=0.1, k=50, query_ids=None, walk_begin=0, walk_end=0):
+    """Packs query nodes (and per-query eps/k/query_id, scalars or sequences) into a Query array."""
+    nodes = np.asarray(nodes, dtype=np.int64).ravel()
+    nq = nodes.size
+    arr = (Query * nq)()
+    eps = np.broadcast_to(np.asarray(eps, dtype=np.float64), (nq,))
+    k = np.broadcast_to(np.asarray(k, dtype=np.int64), (nq,))
+    qid = np.arange(nq, dtype=np.int64) if query_ids is None else np.broadcast_to(np.asarray(query_ids), (nq,))
+    wb = np.broadcast_to(np.asarray(walk_begin), (nq,))
+    we = np.broadcast_to(np.asarray(walk_end), (nq,))
+    for i in range(nq):
+        arr[i] = Query(int(nodes[i]), int(k[i]), float(eps[i]), int(qid[i]) & 0xFFFFFFFF, int(wb[i]), int(we[i]))
+    return arr
+
+
+class Graph:
+    """A device-resident graph store with ProbeSim queries over it."""
+
+    def __init__(self, n, src, dst, config=None, stream=None, **cfg_kw):
+        L = load()
+        self.n = int(n)
+        cfg = config if config is not None else default_config(**cfg_kw)
+        src = _int32(src)
+        dst = _int32(dst)
+        m = int(src.numel() if _is_torch(src) else src.size)
+        h = C.c_void_p()
+        _check(L.probesim_graph_create(self.n, _ptr(src), _ptr(dst), m, C.byref(cfg), _stream(stream), C.byref(h)))
+        self._h = h
+        self.config = cfg
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().probesim_graph_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 -- interpreter shutdown
+            pass
+
+    def info(self):
+        n, m, ep = C.c_int32(), C.c_int64(), C.c_uint64()
+        _check(load().probesim_graph_info(self._h, C.byref(n), C.byref(m), C.byref(ep)))
+        return n.value, m.value, ep.value
+
+    def num_walks(self, eps):
+        r = C.c_int64()
+        _check(load().probesim_num_walks(self._h, float(eps), C.byref(r)))
+        return r.value
+
+    def insert_edges(self, src, dst, stream=None):
+        src, dst = _int32(src), _int32(dst)
+        k = int(src.numel() if _is_torch(src) else src.size)
+        a = C.c_int64()
+        _check(load().probesim_insert_edges(self._h, _ptr(src), _ptr(dst), k, C.byref(a), _stream(stream)))
+        return a.value
+
+    def delete_edges(self, src, dst, stream=None):
+        src, dst = _int32(src), _int32(dst)
+        k = int(src.numel() if _is_torch(src) else src.size)
+        a = C.c_int64()
+        _check(load().probesim_delete_edges(self._h, _ptr(src), _ptr(dst), k, C.byref(a), _stream(stream)))
+        return a.value
+
+    def sample_walks(self, queries, stream=None):
+        """Walk node sequences of the queries: (nodes [W, l_max] int32 padded with -1, lens [W])."""
+        W = 0
+        for q in queries:
+            nr = self.num_walks(q.eps)
+            kb = max(0, q.walk_begin)
+            ke = nr if q.walk_end <= 0 else min(q.walk_end, nr)
+            W += max(0, ke - kb)
+        lm = self.config.l_max
+        nodes = np.zeros((max(1, W), lm), np.int32)
+        lens = np.zeros(max(1, W), np.int32)
+        _check(load().probesim_sample_walks(self._h, queries, len(queries), _ptr(nodes), _ptr(lens), W,
+                                            _stream(stream)))
+        return nodes[:W], lens[:W]
+
+    def single_source(self, queries, out=None, stream=None):
+        """s~(u, .) for every query: a [nq, n] float32 array (numpy) or the given ``out`` buffer."""
+        nq = len(queries)
+        if out is None:
+            out = np.zeros((nq, self.n), np.float32)
+        _check(load().probesim_single_source(self._h, queries, nq, _ptr(out), _stream(stream)))
+        return out
+
+    def topk(self, queries, kmax=None, ids=None, vals=None, stream=None):
+        nq = len(queries)
+        kmax = int(kmax or max(q.k for q in queries))
+        if ids is None:
+            ids = np.zeros((nq, kmax), np.int32)
+        if vals is None:
+            vals = np.zeros((nq, kmax), np.float32)
+        _check(load().probesim_topk(self._h, queries, nq, kmax, _ptr(ids), _ptr(vals), _stream(stream)))
+        return ids, vals
+
+    def set_profiling(self, on=True):
+        _check(load().probesim_set_profiling(self._h, 1 if on else 0))
+
+    def stats(self):
+        s = Stats()
+        _check(load().probesim_get_stats(self._h, C.byref(s)))
+        return s.as_dict()
