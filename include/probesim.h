@@ -140,6 +140,25 @@ typedef struct {
 probesim_status probesim_set_profiling(probesim_graph *g, int32_t on);
 probesim_status probesim_get_stats(const probesim_graph *g, probesim_stats *out);
 
+/* Top-k selection that allocates no memory.  The paper has no counterpart: this serves callers that cannot
+ * allocate device memory while they run, such as a component that has reserved all device memory for its own
+ * pool, or a serving loop that must not take the device-wide synchronisation cudaMalloc and cudaFree imply.
+ * It selects, for each of nq score rows, the kmax-bounded top-k that probesim_topk returns (ordered by score
+ * descending then id ascending, node u excluded, entries r >= ks[i] set to -1 / 0):
+ *   scores  device memory, nq * n FP32 scores, row i for query node nodes[i] (e.g. probesim_single_source output)
+ *   nodes   host array of nq query nodes in [0, n) (excluded from their row's ranking)
+ *   ks      host array of nq result counts in [1, kmax]
+ *   ids     device memory, nq * kmax int32 results;  vals  device memory, nq * kmax FP32 results
+ * Limits: 1 <= nq <= 64, 1 <= kmax <= min(1024, n-1), n >= 2; larger requests fail with PROBESIM_E_INVALID
+ * and a message naming the limit.  The scratch is one fixed __device__ array of 853,504 bytes in the library,
+ * which every GPU that loads the library holds until the process exits.  No call allocates: no cudaMalloc,
+ * cudaFree or allocating library routine is used.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call before any stream capture.
+ * Every call shares the array, and calls serialise on the host and synchronise `stream` before they return;
+ * calls that would overlap on the GPU (for instance from several processes sharing a context) race on it. */
+probesim_status probesim_topk_select_noalloc(const float *scores, int32_t n, int32_t nq, const int32_t *nodes,
+                                             const int32_t *ks, int32_t kmax, int32_t *ids, float *vals, void *stream);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *probesim_last_error(void);
 

@@ -138,6 +138,9 @@ int topk_blocks_per_query(int32_t n);
 void launch_topk(int32_t n, int32_t B, const float *scores, const int32_t *qnode, const int32_t *qk, int32_t kmax,
                  TopkScratch sc, int32_t *ids, float *vals, cudaStream_t s, int64_t *launches);
 
+// sets the message probesim_last_error() returns on the calling thread
+void set_last_error(const char *msg);
+
 // pull tile width for a vector count
 int32_t pull_tile_for(int32_t S);
 inline int32_t round_up(int32_t x, int32_t a) { return (x + a - 1) / a * a; }

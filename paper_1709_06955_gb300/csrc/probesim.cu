@@ -19,6 +19,8 @@ using namespace ps;
 // ------------------------------------------------------------------------------------------------
 static thread_local std::string g_last_error;
 
+void ps::set_last_error(const char *msg) { g_last_error = msg; }
+
 static probesim_status fail(probesim_status st, const std::string &msg) {
     g_last_error = msg;
     return st;

@@ -19,7 +19,7 @@ EXPORTS = [
     "probesim_config_default", "probesim_graph_create", "probesim_graph_destroy", "probesim_graph_info",
     "probesim_insert_edges", "probesim_delete_edges", "probesim_num_walks", "probesim_sample_walks",
     "probesim_single_source", "probesim_topk", "probesim_set_profiling", "probesim_get_stats",
-    "probesim_last_error",
+    "probesim_last_error", "probesim_topk_select_noalloc",
 ]
 
 
@@ -75,6 +75,7 @@ def load(path=None):
     L.probesim_topk.argtypes = [vp, P(Query), C.c_int32, C.c_int32, vp, vp, vp]
     L.probesim_set_profiling.argtypes = [vp, C.c_int32]
     L.probesim_get_stats.argtypes = [vp, P(Stats)]
+    L.probesim_topk_select_noalloc.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp, vp]
     for name in EXPORTS:
         if name != "probesim_last_error":
             getattr(L, name).restype = C.c_int
@@ -141,6 +142,20 @@ def make_queries(nodes, eps=0.1, k=50, query_ids=None, walk_begin=0, walk_end=0)
     for i in range(nq):
         arr[i] = Query(int(nodes[i]), int(k[i]), float(eps[i]), int(qid[i]) & 0xFFFFFFFF, int(wb[i]), int(we[i]))
     return arr
+
+
+def topk_select_noalloc(scores, nodes, ks, kmax, ids, vals, stream=None):
+    """Top-k of caller-provided device score rows without any allocation (probesim_topk_select_noalloc).
+
+    For callers that cannot allocate device memory while they run.  ``scores`` is a CUDA tensor [nq, n];
+    ``ids`` / ``vals`` are CUDA tensors [nq, kmax] (int32 / float32) that receive the results; ``nodes`` and
+    ``ks`` are host sequences of length nq.  At most 64 queries and kmax <= 1024 per call."""
+    nq, n = int(scores.shape[0]), int(scores.shape[1])
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+    ks = np.ascontiguousarray(ks, dtype=np.int32)
+    _check(load().probesim_topk_select_noalloc(_ptr(scores), n, nq, _ptr(nodes), _ptr(ks), int(kmax), _ptr(ids),
+                                               _ptr(vals), _stream(stream)))
+    return ids, vals
 
 
 class Graph:
