@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=12.0, help="Poisson arrival rate of the serving leg (q/s)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the serving leg")
     return ap.parse_args()
 
 
@@ -151,6 +153,32 @@ def cpu_baseline(n, s, d, qs, budget_s):
                       "queries/s extrapolated from the time per walk" % (k - 1, nr, WORKLOAD, el)}
 
 
+def serving_leg(probesim, G, qs, rate, seconds, rank):
+    """Queries arrive as a Poisson process at `rate` q/s for `seconds`; returns latency and throughput."""
+    import numpy as np
+    S = probesim.Server(G, workers=2, max_batch=8, kmax=100)
+    rng = np.random.default_rng(4 + rank)
+    gaps = rng.exponential(1.0 / rate, size=int(rate * seconds * 3) + 10)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < seconds]
+    ks = np.array([10, 50, 100])[rng.integers(0, 3, arrivals.size)]
+    t0 = time.perf_counter()
+    done = 0
+    for i, ta in enumerate(arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        S.submit(probesim.make_queries([qs[i % len(qs)]], eps=EPS, k=int(ks[i]), query_ids=[900000 + i]))
+        done += len(S.poll(64, wait_ms=0))
+    while done < arrivals.size:
+        done += len(S.poll(64, wait_ms=500))
+    st = S.stats()
+    S.close()
+    return {"arrival_rate_qps": rate, "queries": int(arrivals.size), "qps": st["qps"], "p50_ms": st["p50_ms"],
+            "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"], "workers": 2, "max_batch": 8,
+            "k": "uniform {10, 50, 100}", "eps": EPS}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -221,6 +249,7 @@ def run_ours(args):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     agg = {"probe_ms": 0.0, "probe_bytes": 0.0, "probe_launches": 0, "kernel_launches": 0, "edge_gathers": 0,
            "vectors": 0, "tree_nodes": 0, "walks": 0}
+    phases = {}
     with ClockSampler(local) as clk:
         barrier()
         w0 = time.perf_counter()
@@ -232,6 +261,8 @@ def run_ours(args):
             st = G.stats()
             for k in agg:
                 agg[k] += st[k]
+            for k, v in st["phase_ms"].items():
+                phases[k] = phases.get(k, 0.0) + v
         barrier()
         wall = time.perf_counter() - w0
     G.set_profiling(False)
@@ -263,6 +294,9 @@ def run_ours(args):
     barrier()
     bms = sum(a.elapsed_time(b) for a, b in bev)
     batched_qps = nb * B / (bms / 1e3)
+
+    # serving leg: Poisson arrivals into the continuous-batching server (top-k, k in {10, 50, 100})
+    serving = serving_leg(probesim, G, qs, args.serve_rate, args.serve_seconds, rank)
 
     # end-to-end through the C ABI with host buffers: query struct in, pinned host scores out
     host_out = torch.empty((1, n), dtype=torch.float32, pin_memory=True)
@@ -310,6 +344,8 @@ def run_ours(args):
             "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": 32, "d2h_bytes_per_step": 4 * n,
                     "steps": e2e_steps},
             "roofline": roof, "clocks": clk.summary(), "gpu_launches": agg["kernel_launches"],
+            "phases_ms_per_query": {k: v / args.steps for k, v in phases.items()},
+            "serving": serving,
             "work": {"walks_per_query": agg["walks"] / args.steps, "tree_nodes_per_query": agg["tree_nodes"] / args.steps,
                      "vectors_per_query": agg["vectors"] / args.steps,
                      "edge_gathers_per_query": agg["edge_gathers"] / args.steps}}

@@ -135,10 +135,68 @@ typedef struct {
     double probe_bytes;     /* algorithmic bytes of those launches: 4 per edge index and 4 per gathered
                                score per vector-edge, 4 per written score, 12 per vertex per tile */
     int64_t kernel_launches;/* all kernels this library launched in the call */
+    double phase_ms[12];    /* profiling on: CUDA-event time per phase of the deterministic path: 0 walks,
+                               1 walk tree and level schedule, 2 D build, 3 gamma scatter, 4 split-row zeroing,
+                               5 pull, 6 push columns, 7 gamma, 8 estimates; 9-11 unused */
 } probesim_stats;
 
 probesim_status probesim_set_profiling(probesim_graph *g, int32_t on);
 probesim_status probesim_get_stats(const probesim_graph *g, probesim_stats *out);
+
+/* ---------------------------------------------------------------------------------------------------------
+ * Serving loop (continuous batching).  Queries and edge-update batches enter one FIFO.  `workers` threads,
+ * each with its own scratch memory and CUDA stream, take the next batch of queries from the head as soon as
+ * they are free: up to max_batch queries, admitted while the estimated score-buffer memory of the batches in
+ * flight (about 12 * n * 0.25 * n_r bytes per query) stays within memory_budget_bytes.  Queries that arrive
+ * while other batches run are admitted by the next free worker, so the work of several batches overlaps on
+ * the device.  An update batch at the head is applied between batches: queries submitted after it see the
+ * new edge set, queries submitted before it the old one.  Results are top-k lists (Def. 2).
+ * --------------------------------------------------------------------------------------------------------- */
+typedef struct probesim_server probesim_server;
+
+typedef struct {
+    int32_t workers;            /* concurrent batch pipelines, 1..8 */
+    int32_t max_batch;          /* queries per batch, 1..4096 */
+    int32_t kmax;               /* largest k a query may ask for, 1..min(4096, n-1) */
+    int32_t queue_capacity;     /* queries waiting at once; submit beyond it fails with PROBESIM_E_BUSY */
+    double memory_budget_bytes; /* score-buffer memory admitted at once; 0 = 60% of device memory */
+} probesim_server_config;
+
+typedef struct {
+    uint64_t ticket;     /* returned by probesim_server_submit */
+    uint32_t query_id;
+    int32_t node, k;
+    int32_t status;      /* probesim_status of the batch that ran the query */
+    uint64_t epoch;      /* update epoch of the edge set the query saw */
+    int32_t batch_size;  /* queries in its batch */
+    int32_t worker;      /* worker that ran it */
+    double queue_ms;     /* submit -> batch start */
+    double latency_ms;   /* submit -> result ready */
+} probesim_result;
+
+typedef struct {
+    int64_t submitted, completed, rejected, failed, batches, updates_applied;
+    double mean_batch;   /* queries per batch */
+    double p50_ms, p99_ms, mean_ms;  /* latency of completed queries */
+    double qps;          /* completed queries / (last completion - first submit) */
+} probesim_server_stats;
+
+/* workers = 2, max_batch = 16, kmax = 100, queue_capacity = 100000, memory_budget_bytes = 0. */
+probesim_status probesim_server_config_default(probesim_server_config *cfg);
+/* Starts the workers over graph g (which must outlive the server). */
+probesim_status probesim_server_create(probesim_graph *g, const probesim_server_config *cfg, probesim_server **out);
+/* Enqueues nq queries (host array, k <= kmax); tickets (host, may be NULL) receives their tickets. */
+probesim_status probesim_server_submit(probesim_server *s, const probesim_query *q, int32_t nq, uint64_t *tickets);
+/* Enqueues an update batch of k edges (host arrays); insert != 0 inserts, 0 deletes (see probesim_insert_edges). */
+probesim_status probesim_server_update(probesim_server *s, const int32_t *src, const int32_t *dst, int64_t k,
+                                       int32_t insert);
+/* Moves up to max_results finished results into res, with their top-k in ids/vals ([max_results][kmax], host),
+ * waiting up to wait_ms for the first one; *count receives the number moved. */
+probesim_status probesim_server_poll(probesim_server *s, int32_t max_results, int32_t kmax, probesim_result *res,
+                                     int32_t *ids, float *vals, int32_t *count, int32_t wait_ms);
+probesim_status probesim_server_get_stats(probesim_server *s, probesim_server_stats *out);
+/* Stops the workers after their current batches; queries still waiting are dropped. */
+probesim_status probesim_server_destroy(probesim_server *s);
 
 /* Top-k selection that allocates no memory.  The paper has no counterpart: this serves callers that cannot
  * allocate device memory while they run, such as a component that has reserved all device memory for its own

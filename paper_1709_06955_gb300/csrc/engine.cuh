@@ -1,0 +1,125 @@
+// Host-side engine types shared by the C ABI (probesim.cu) and the serving loop (server.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+#include <shared_mutex>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+// ------------------------------------------------------------------------------------------------
+// device buffers that grow on demand and are freed with the graph
+// ------------------------------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        const size_t nb = std::max<size_t>(256, bytes + bytes / 8);
+        cudaError_t e = cudaMalloc(&p, nb);
+        if (e == cudaSuccess) cap = nb; else cudaGetLastError();
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+struct PinnedBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap && p) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t nb = std::max<size_t>(256, bytes + bytes / 8);
+        cudaError_t e = cudaMallocHost(&p, nb);
+        if (e == cudaSuccess) cap = nb; else cudaGetLastError();
+        return e;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// Per-call device and pinned buffers; a graph owns one for direct calls, a server one per worker.
+struct Workspace {
+    DevBuf qbuf, walks, lens, ctr;
+    DevBuf t_key, t_node, t_parent, t_depth, t_query, t_weight, t_height, t_slot, t_gamma, t_G;
+    DevBuf counts, offs, node_list, slot_entry, nchild, child_off, child_list, ccur, rho_slot;
+    DevBuf md_a, md_b, dmat, out_stage;
+    DevBuf r_cnt, r_off, r_part, r_iwalk, r_ilen, r_iq, r_ik, r_fi[2], r_fn[2], r_keys[2], r_deg, r_pref, r_counts, r_ctr;
+    DevBuf tk_hist, tk_state, tk_tie, tk_cid, tk_cval, tk_ids, tk_vals, tk_qk;
+    PinnedBuf pin_q;  // query arrays of one batch
+    PinnedBuf pin_s;  // counters and schedule offsets (fixed size, allocated at creation)
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev;
+    probesim_stats stats{};
+    void release() {
+        DevBuf *bufs[] = {&qbuf, &walks, &lens, &ctr, &t_key, &t_node, &t_parent, &t_depth, &t_query, &t_weight,
+                          &t_height, &t_slot, &t_gamma, &t_G, &counts, &offs, &node_list, &slot_entry, &nchild,
+                          &child_off, &child_list, &ccur, &rho_slot, &md_a, &md_b, &dmat, &out_stage, &r_cnt, &r_off,
+                          &r_part, &r_iwalk, &r_ilen, &r_iq, &r_ik, &r_fi[0], &r_fi[1], &r_fn[0], &r_fn[1],
+                          &r_keys[0], &r_keys[1], &r_deg, &r_pref, &r_counts, &r_ctr, &tk_hist, &tk_state, &tk_tie,
+                          &tk_cid, &tk_cval, &tk_ids, &tk_vals, &tk_qk};
+        for (DevBuf *b : bufs) b->release();
+        pin_q.release();
+        pin_s.release();
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        ev.clear();
+    }
+};
+
+struct probesim_graph {
+    std::mutex mu;              // serialises direct calls (they share ws0)
+    std::shared_mutex store_mu; // queries read the store shared; update batches take it exclusively
+    probesim_config cfg{};
+    uint32_t t_stop = 0;
+    uint32_t t_keep = 0;
+    int device = 0;
+    ps::DeviceGraph dg;
+    // device arrays of the graph store
+    DevBuf in_off, in_col, out_off, out_col, w, piece_v, piece_beg, piece_len, split_v, ext2int, int2ext;
+    // sorted keys (dst << 32 | src) of the initial edge set, freed once the store is built
+    std::vector<uint64_t> keys;
+    std::vector<int32_t> h_ext2int;  // host copy of the id map (update batches are sorted by internal ids)
+    // update scratch
+    DevBuf u_batch, u_valid, u_vpre, u_delta, u_deg, u_part, u_hist;
+    uint64_t epoch = 0;
+    Workspace ws0;
+    size_t budget = 0;
+};
+
+
+namespace ps {
+// Status helpers (probesim.cu): set the calling thread's message and return the status.
+probesim_status fail_status(probesim_status st, const std::string &msg);
+// Checks a query array against the graph (ids, eps, k <= kmax when topk).
+probesim_status check_queries(const probesim_graph *g, const probesim_query *q, int32_t nq, bool topk, int32_t kmax);
+// Estimates and top-k of nq queries with workspace ws on stream st.  The caller owns ws and holds
+// g->store_mu shared.
+probesim_status single_source_core(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t nq,
+                                   float *scores, cudaStream_t st);
+probesim_status topk_core(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t nq, int32_t kmax,
+                          int32_t *ids, float *vals, cudaStream_t st);
+// Applies one update batch (takes g->store_mu exclusively).
+probesim_status apply_updates(probesim_graph *g, const int32_t *src, const int32_t *dst, int64_t k, bool insert,
+                              int64_t *applied, cudaStream_t st);
+int64_t num_walks_for(const probesim_graph *g, double eps);
+}  // namespace ps

@@ -47,7 +47,7 @@ __device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
 // decomposition of the pull kernel: every in-list cut into pieces of at most kPiece edges, ordered
 // by length (longest first).  A piece of a vertex cut into several pieces is added atomically.
 // ---------------------------------------------------------------------------------------------
-constexpr int kPiece = 64;
+constexpr int kPiece = 128;
 
 struct DeviceGraph {
     int32_t n = 0;
@@ -63,12 +63,14 @@ struct DeviceGraph {
     int32_t *piece_len = nullptr;  // length | (split ? 1 << 31 : 0)
     int32_t n_split = 0;           // vertices cut into more than one piece
     int32_t *split_v = nullptr;
+    int32_t *ext2int = nullptr;    // caller's node id -> internal id (descending out-degree order)
+    int32_t *int2ext = nullptr;    // internal id -> caller's node id
 };
 
 // The queries of one launch.
 struct QueryBatch {
     int32_t B = 0;
-    const int32_t *node = nullptr;     // u per query
+    const int32_t *node = nullptr;     // u per query (caller's id; the kernels map it)
     const uint32_t *qid = nullptr;     // Philox key word 1 per query
     const int32_t *walk_base = nullptr;  // [B+1] prefix sums of walk counts
     const int32_t *walk_k0 = nullptr;  // index of the first walk per query
@@ -87,7 +89,8 @@ struct TrieTable {
     int32_t *query = nullptr;  // query index in the launch
     int32_t *weight = nullptr; // walks sharing the prefix
     int32_t *height = nullptr; // longest path below the node
-    int32_t *slot = nullptr;   // column of the node's score vector at its depth, -1 if it has none
+    int32_t *slot = nullptr;   // column of the node's score vector at its depth (dense columns first, then
+                               // push columns), -1 if it has none
     float *gamma = nullptr;    // normalised weight minus the excluded score (see probe_level.cu)
     float *G = nullptr;        // sum of the children's gamma
 };
@@ -109,8 +112,8 @@ void launch_walks(const DeviceGraph &g, const QueryBatch &q, int32_t W, int32_t 
                   uint32_t seed, int32_t *walks, int32_t *lens, bool pad, LaunchCounters *ctr, cudaStream_t s);
 void launch_trie_insert(const DeviceGraph &g, const QueryBatch &q, int32_t W, int32_t l_max, const int32_t *walks,
                         const int32_t *lens, TrieTable t, LaunchCounters *ctr, cudaStream_t s);
-void launch_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, cudaStream_t s);
-void launch_sched_lists(TrieTable t, const int32_t *node_off, const int32_t *slot_off, int32_t *ncur,
+void launch_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, int32_t *hcount, cudaStream_t s);
+void launch_sched_lists(TrieTable t, const int32_t *node_off, const int32_t *slot_off, const int32_t *dw, int32_t *ncur,
                         int32_t *node_list, int32_t *slot_entry, int32_t *nchild, int32_t *rho_slot, cudaStream_t s);
 void launch_scan_exclusive(const int32_t *in, int32_t *out, int32_t count, cudaStream_t s);  // out has count+1
 void launch_sched_children(TrieTable t, const int32_t *slot_entry, int32_t S_total, const int32_t *slot_off,
@@ -118,13 +121,20 @@ void launch_sched_children(TrieTable t, const int32_t *slot_entry, int32_t S_tot
 
 void launch_dbuild(int32_t n, const float *MDp, int32_t pp, float *D, int32_t pd, int32_t S, const int32_t *child_off,
                    const int32_t *child_list, cudaStream_t s);
-void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, int32_t pd, cudaStream_t s);
-void launch_zero_split_rows(const DeviceGraph &g, float *MD, int32_t pitch, cudaStream_t s);
-void launch_pull(const DeviceGraph &g, const float *D, float *MD, int32_t pitch, int32_t tile, cudaStream_t s);
+void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, int32_t pd, int32_t dw,
+                          cudaStream_t s);
+void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, int32_t pitch,
+                    int32_t dw, cudaStream_t s);
+void launch_zero_cols(int32_t n, float *MD, int32_t pitch, int32_t c0, int32_t width, cudaStream_t s);
+void launch_zero_split_rows(const DeviceGraph &g, float *MD, int32_t pitch, int32_t width, cudaStream_t s);
+void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, float *MD, int32_t pitch, int32_t tile,
+                 cudaStream_t s);
 void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, const float *inv_nr,
                   const float *MD, int32_t pc, cudaStream_t s);
 void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,
-                     int32_t p0, float *out, cudaStream_t s);
+                     int32_t p0, const int32_t *ext2int, float *out, cudaStream_t s);
+// ids[i] = map[ids[i]] for ids[i] >= 0
+void launch_map_ids(int32_t *ids, int64_t count, const int32_t *map, cudaStream_t s);
 
 // top-k: scores [B][n] on the device; ids/vals [B][kmax]
 struct TopkScratch {
@@ -137,6 +147,58 @@ struct TopkScratch {
 int topk_blocks_per_query(int32_t n);
 void launch_topk(int32_t n, int32_t B, const float *scores, const int32_t *qnode, const int32_t *qk, int32_t kmax,
                  TopkScratch sc, int32_t *ids, float *vals, cudaStream_t s, int64_t *launches);
+
+// randomized PROBE (rand_probe.cu)
+struct RandLevel {
+    const int32_t *fr_inst = nullptr, *fr_node = nullptr;  // frontier H_j (entries with out-edges)
+    int64_t F = 0;
+    const long long *prefix = nullptr;  // [F+1] out-degree prefix sums
+    int64_t E = 0;                      // work items (frontier out-edges)
+    const unsigned long long *cur_keys = nullptr;  // set of (instance, node) in H_j
+    int64_t cur_cap = 0;
+    unsigned long long *next_keys = nullptr;       // set of (instance, node) in H_{j+1}
+    int64_t next_cap = 0;
+    int32_t *next_inst = nullptr, *next_node = nullptr;  // H_{j+1} entries with out-edges
+    unsigned long long *next_count = nullptr;
+    int32_t *counts = nullptr;          // [B][n] members of H_{i-1} per query (internal ids)
+    int32_t *overflow = nullptr;
+    int32_t j = 0;
+};
+int64_t scan64_partials_needed(int64_t count);
+void launch_scan64(const long long *in, int64_t count, long long *partial, long long *out, cudaStream_t s);
+void launch_inst_count(const int32_t *lens, int32_t W, long long *cnt, cudaStream_t s);
+void launch_inst_init(const QueryBatch &q, const DeviceGraph &g, const int32_t *lens, int32_t W, int32_t l_max,
+                      const int32_t *walks, const long long *inst_off, int32_t *inst_walk, int32_t *inst_len,
+                      int32_t *inst_q, uint32_t *inst_k, int32_t *fr_inst, int32_t *fr_node,
+                      unsigned long long *fr_count, unsigned long long *keys, int64_t cap, int32_t *overflow,
+                      cudaStream_t s);
+void launch_frontier_degree(const int32_t *fr_inst, const int32_t *fr_node, int64_t F, const int32_t *inst_len, int32_t j,
+                            const int64_t *out_off, long long *deg, cudaStream_t s);
+void launch_rand_level(const DeviceGraph &g, const int32_t *walks, int32_t l_max, const int32_t *inst_walk,
+                       const int32_t *inst_len, const int32_t *inst_q, const uint32_t *inst_k, const uint32_t *qkey,
+                       uint32_t seed, uint32_t t_keep, const RandLevel &L, cudaStream_t s);
+void launch_rand_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *counts, const float *inv_nr,
+                          const int32_t *ext2int, float *out, cudaStream_t s);
+
+// device-side graph updates (graph_update.cu)
+struct UpdateBatchArgs {
+    int64_t k = 0;
+    const int32_t *in_dst = nullptr, *in_src = nullptr, *in_src_ext = nullptr;  // sorted by (dst, src ext)
+    const int32_t *out_src = nullptr, *out_dst = nullptr;                         // sorted by (src, dst)
+    long long *in_valid = nullptr, *out_valid = nullptr;
+    const long long *in_vpre = nullptr, *out_vpre = nullptr;
+    bool insert = true;
+};
+void launch_upd_mark(const DeviceGraph &g, const UpdateBatchArgs &a, long long *in_delta, long long *out_delta,
+                     cudaStream_t s);
+void launch_upd_degrees(int32_t n, const int64_t *off, const long long *delta, long long *deg, cudaStream_t s);
+void launch_upd_rows(const DeviceGraph &g, const UpdateBatchArgs &a, bool in_lists, const long long *new_off,
+                     int32_t *new_col, cudaStream_t s);
+void launch_upd_w(int32_t n, const long long *new_off, float sqrt_c, float *w, long long *npieces, cudaStream_t s);
+void launch_upd_pieces(int32_t n, const long long *new_off, unsigned long long *hist, unsigned long long *cursor,
+                       int32_t *split_v, unsigned long long *n_split, int32_t *pv, int64_t *pb, int32_t *pl,
+                       cudaStream_t s);
+void launch_i64_copy(const long long *a, int64_t *b, int64_t count, cudaStream_t s);
 
 // sets the message probesim_last_error() returns on the calling thread
 void set_last_error(const char *msg);

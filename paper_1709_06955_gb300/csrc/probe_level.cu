@@ -9,15 +9,20 @@
 //     X_a M C = M C - beta e_a,   beta = (M C)[a] = sqrt(c)/|I(a)| * sum_{x in I(a)} C[x],
 // so with gamma_s = w_s/n_r - beta_s the children of one tree node share one application of M:
 //     C(t) = M D(t) + sum_s gamma_s e_{a_s},  D(t) = sum over children s of C(s).
-// A tree node whose subtree has height >= 2 owns a dense score vector MD(t) = M D(t) (a "slot");
-// lower nodes only contribute their sparse gamma terms.  The level loop runs from the deepest depth to
-// the virtual super-root (depth 0, whose only child is the root u):
-//   dbuild   D(t)[x]  = sum of the children's MD columns                (segmented row sums)
-//   scatter  D(t)[a_g] += gamma_g for every grandchild g of t            (sparse terms)
-//   pull     MD(t)[v] = sqrt(c)/|I(v)| * sum_{x in I(v)} D(t)[x]         (the dominant kernel)
+// A tree node whose subtree has height >= 2 owns a score vector MD(t) = M D(t) (a column); lower nodes
+// only contribute their sparse gamma terms.  For height >= 3 the column is "dense" and computed by the
+// pull; for height 2, D(t) is just the gamma terms of t's grandchildren (all leaves), so the column is
+// "pushed": MD(t) = sum_g gamma_g * sum_{x in O(a_g)} sqrt(c)/|I(x)| e_x.  The level loop runs from the
+// deepest depth to the virtual super-root (depth 0, whose only child is the root u):
+//   dbuild   D(t)[x]  = sum of the children's MD columns                (segmented row sums, dense t)
+//   scatter  D(t)[a_g] += gamma_g for every grandchild g of t            (sparse terms, dense t)
+//   pull     MD(t)[v] = sqrt(c)/|I(v)| * sum_{x in I(v)} D(t)[x]         (the dominant kernel, dense t)
+//   push     MD(t)[x] += sqrt(c)/|I(x)| * gamma_g, x in O(a_g)           (height-2 t)
 //   gamma    gamma_t  = w_t/n_r - sqrt(c)/|I(a_t)| * (sum_{x in I(a_t)} MD(t)[x] + G_t),  G_parent += gamma_t
 // The result is exactly Alg. 4's (up to FP32 rounding); the work is one pull per slot instead of
 // q-1 pushes per tree node.  Score vectors of one depth are stored node-major, [n][pitch] FP32.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace ps {
@@ -56,43 +61,149 @@ static int grid_for(int64_t work, int threads, int per_sm) {
     return (int)(blocks < 1 ? 1 : blocks);
 }
 
+// dbuild through shared memory: a block copies R consecutive rows of MDp (one contiguous range of about 32 KB,
+// whatever the width) into shared memory and forms the R output rows of D (one contiguous range) from it,
+// one output element per thread and step; the depth's child lists sit in shared memory.  Both global
+// transfers are fully coalesced.
+constexpr int kDbThreads = 256;
+
+__global__ void __launch_bounds__(kDbThreads) k_dbuild_smem(int32_t n, const float *__restrict__ MDp, int32_t pp,
+                                                            float *__restrict__ D, int32_t pd, int32_t S,
+                                                            const int32_t *__restrict__ child_off,
+                                                            const int32_t *__restrict__ child_list, int32_t R) {
+    extern __shared__ float sm[];
+    float *rows = sm;
+    int32_t *s_off = reinterpret_cast<int32_t *>(sm + (size_t)R * pp);
+    int32_t *s_list = s_off + (S + 1);
+    const int32_t base = child_off[0], nk = child_off[S] - base;
+    for (int32_t i = threadIdx.x; i <= S; i += blockDim.x) s_off[i] = child_off[i] - base;
+    for (int32_t i = threadIdx.x; i < nk; i += blockDim.x) s_list[i] = child_list[base + i];
+    __syncthreads();
+    for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < n; r0 += (int64_t)gridDim.x * R) {
+        const int32_t nr = (int32_t)min((int64_t)R, (int64_t)n - r0);
+        const int32_t cnt = nr * pp;
+        const float *src = MDp + r0 * pp;
+        if ((pp & 3) == 0) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+            float4 *d4 = reinterpret_cast<float4 *>(rows);
+            for (int32_t i = threadIdx.x; i < cnt / 4; i += blockDim.x) d4[i] = __ldcs(s4 + i);
+        } else {
+            for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) rows[i] = __ldcs(src + i);
+        }
+        __syncthreads();
+        float *dst = D + r0 * pd;
+        const int32_t ocnt = nr * pd;
+        for (int32_t o = threadIdx.x; o < ocnt; o += blockDim.x) {
+            const int32_t r = o / pd, p = o - r * pd;
+            float acc = 0.f;
+            if (p < S) {
+                const float *row = rows + r * pp;
+                const int32_t ce = s_off[p + 1];
+                for (int32_t c = s_off[p]; c < ce; ++c) acc += row[s_list[c]];
+            }
+            __stcs(dst + o, acc);
+        }
+        __syncthreads();
+    }
+}
+
 void launch_dbuild(int32_t n, const float *MDp, int32_t pp, float *D, int32_t pd, int32_t S, const int32_t *child_off,
                    const int32_t *child_list, cudaStream_t s) {
+    // rows per block step: about 32 KB of MDp rows at any width; the child lists need (S + 1 + children) ints,
+    // children <= pp
+    const int32_t R = (int32_t)std::max<int64_t>(1, std::min<int64_t>(4096, 8192 / std::max(1, pp)));
+    const int64_t smem = 4 * (int64_t)R * pp + 4 * ((int64_t)S + 1 + pp);
+    if (smem <= 160 * 1024 && (int64_t)R * std::max(pp, pd) < ((int64_t)1 << 30)) {
+        cudaFuncSetAttribute(k_dbuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        const int blocks = grid_for((int64_t)(n + R - 1) / R * kDbThreads, kDbThreads, 4);
+        k_dbuild_smem<<<blocks, kDbThreads, (size_t)smem, s>>>(n, MDp, pp, D, pd, S, child_off, child_list, R);
+        return;
+    }
     const int blocks = grid_for((int64_t)n * 32, 256, 8);
     k_dbuild<<<blocks, 256, 0, s>>>(n, MDp, pp, D, pd, S, child_off, child_list);
 }
 
+// zero columns [c0, c0 + width) of every row: one warp per row
+__global__ void __launch_bounds__(256) k_zero_cols(int32_t n, float *MD, int32_t pitch, int32_t c0, int32_t width) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        float *row = MD + v * pitch + c0;
+        for (int32_t c = lane; c < width; c += 32) row[c] = 0.f;
+    }
+}
+
+void launch_zero_cols(int32_t n, float *MD, int32_t pitch, int32_t c0, int32_t width, cudaStream_t s) {
+    if (width <= 0) return;
+    const int blocks = grid_for((int64_t)n * 32, 256, 8);
+    k_zero_cols<<<blocks, 256, 0, s>>>(n, MD, pitch, c0, width);
+}
+
 // ------------------------------------------------------------------------------------------------
-// scatter: for every tree node g at depth t+2, D[a_g][slot(grandparent(g))] += gamma_g.
+// scatter: for every tree node g at depth t+2 whose grandparent has a dense column (< dw),
+// D[a_g][slot(grandparent(g))] += gamma_g.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_scatter_gamma(const int32_t *__restrict__ nodes, int32_t cnt, TrieTable t, float *D, int32_t pd) {
+__global__ void k_scatter_gamma(const int32_t *__restrict__ nodes, int32_t cnt, TrieTable t, float *D, int32_t pd,
+                                int32_t dw) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cnt) return;
     const int32_t e = nodes[i];
-    const int32_t gp = t.parent[t.parent[e]];
-    atomicAdd(D + (int64_t)t.node[e] * pd + t.slot[gp], t.gamma[e]);
+    const int32_t sl = t.slot[t.parent[t.parent[e]]];
+    if (sl < 0 || sl >= dw) return;
+    atomicAdd(D + (int64_t)t.node[e] * pd + sl, t.gamma[e]);
 }
 
-void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, int32_t pd, cudaStream_t s) {
+void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, int32_t pd, int32_t dw,
+                          cudaStream_t s) {
     if (cnt <= 0) return;
-    k_scatter_gamma<<<(cnt + 255) / 256, 256, 0, s>>>(nodes, cnt, t, D, pd);
+    k_scatter_gamma<<<(cnt + 255) / 256, 256, 0, s>>>(nodes, cnt, t, D, pd, dw);
+}
+
+// ------------------------------------------------------------------------------------------------
+// push: one warp per tree node g at depth t+2 whose grandparent p has a push column (>= dw):
+// MD[x][slot(p)] += sqrt(c)/|I(x)| * gamma_g for every x in O(a_g).
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_push_h2(const int64_t *__restrict__ out_off, const int32_t *__restrict__ out_col,
+                                                 const float *__restrict__ w, const int32_t *__restrict__ nodes,
+                                                 int32_t cnt, TrieTable t, float *MD, int32_t pitch, int32_t dw) {
+    const int lane = threadIdx.x & 31;
+    const int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= cnt) return;
+    const int32_t e = nodes[i];
+    const int32_t sl = t.slot[t.parent[t.parent[e]]];
+    if (sl < dw) return;
+    const int32_t a = t.node[e];
+    const float g = t.gamma[e];
+    const int64_t beg = out_off[a], end = out_off[a + 1];
+    for (int64_t k = beg + lane; k < end; k += 32) {
+        const int32_t x = __ldg(out_col + k);
+        atomicAdd(MD + (int64_t)x * pitch + sl, __ldg(w + x) * g);
+    }
+}
+
+void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, int32_t pitch,
+                    int32_t dw, cudaStream_t s) {
+    if (cnt <= 0) return;
+    const int64_t threads = (int64_t)cnt * 32;
+    k_push_h2<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(g.out_off, g.out_col, g.w, nodes, cnt, t, MD, pitch, dw);
 }
 
 // ------------------------------------------------------------------------------------------------
 // Rows of vertices whose in-list is cut into several pieces receive atomic adds: zero them first.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_zero_rows(const int32_t *__restrict__ rows, int32_t cnt, float *MD, int32_t pitch) {
+__global__ void k_zero_rows(const int32_t *__restrict__ rows, int32_t cnt, float *MD, int32_t pitch, int32_t width) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)cnt * pitch;
+    const int64_t total = (int64_t)cnt * width;
     if (i >= total) return;
-    const int64_t r = i / pitch, c = i - r * pitch;
+    const int64_t r = i / width, c = i - r * width;
     MD[(int64_t)rows[r] * pitch + c] = 0.f;
 }
 
-void launch_zero_split_rows(const DeviceGraph &g, float *MD, int32_t pitch, cudaStream_t s) {
-    const int64_t total = (int64_t)g.n_split * pitch;
+void launch_zero_split_rows(const DeviceGraph &g, float *MD, int32_t pitch, int32_t width, cudaStream_t s) {
+    const int64_t total = (int64_t)g.n_split * width;
     if (total <= 0) return;
-    k_zero_rows<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g.split_v, g.n_split, MD, pitch);
+    k_zero_rows<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g.split_v, g.n_split, MD, pitch, width);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -145,7 +256,8 @@ template <int T>
 __global__ void __launch_bounds__(256) k_pull(const int32_t *__restrict__ piece_v, const int64_t *__restrict__ piece_beg,
                                               const int32_t *__restrict__ piece_len, int64_t n_pieces,
                                               const int32_t *__restrict__ in_col, const float *__restrict__ w,
-                                              const float *__restrict__ D, float *__restrict__ MD, int32_t pitch) {
+                                              const float *__restrict__ D, int32_t dpitch, float *__restrict__ MD,
+                                              int32_t pitch) {
     constexpr int VEC = T >= 4 ? 4 : T;
     constexpr int L = T / VEC;         // lanes per group
     constexpr int CH = 8;              // in-neighbours per chunk
@@ -174,7 +286,7 @@ __global__ void __launch_bounds__(256) k_pull(const int32_t *__restrict__ piece_
 #pragma unroll
             for (int j = 0; j < CH; ++j) {
                 const int32_t x = L == 1 ? mine[j] : __shfl_sync(gmask, mine[j / L], j % L, L);
-                val[j] = x >= 0 ? VecT<VEC>::load(D + (int64_t)x * pitch + col0) : vzero<V>();
+                val[j] = x >= 0 ? VecT<VEC>::load(D + (int64_t)x * dpitch + col0) : vzero<V>();
             }
 #pragma unroll
             for (int j = 0; j < CH; ++j) vadd(acc, val[j]);
@@ -190,21 +302,24 @@ int32_t pull_tile_for(int32_t S) {
     if (S <= 2) return 2;
     if (S <= 4) return 4;
     if (S <= 8) return 8;
-    return 16;
+    if (S <= 16) return 16;
+    return 32;
 }
 
-void launch_pull(const DeviceGraph &g, const float *D, float *MD, int32_t pitch, int32_t tile, cudaStream_t s) {
-    const int32_t ntiles = pitch / tile;
+void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, float *MD, int32_t pitch, int32_t tile,
+                 cudaStream_t s) {
+    const int32_t ntiles = dpitch / tile;
     const int L = tile >= 4 ? tile / 4 : 1;
     const int64_t threads_needed = g.n_pieces * L;
     const int blocks = grid_for(threads_needed, 256, 8);
     dim3 grid(blocks, ntiles);
     switch (tile) {
-        case 1: k_pull<1><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
-        case 2: k_pull<2><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
-        case 4: k_pull<4><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
-        case 8: k_pull<8><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
-        default: k_pull<16><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, MD, pitch); break;
+        case 1: k_pull<1><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
+        case 2: k_pull<2><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
+        case 4: k_pull<4><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
+        case 8: k_pull<8><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
+        case 16: k_pull<16><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
+        default: k_pull<32><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
     }
 }
 
@@ -246,23 +361,34 @@ void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieT
 }
 
 // ------------------------------------------------------------------------------------------------
-// finalize: out[q][v] = MD0[v][rho_slot(q)], out[q][u_q] = 1 (s(u,u) = 1).
+// finalize: out[q][v] = MD0[ext2int[v]][rho_slot(q)] for the caller's node id v, out[q][u_q] = 1 (s(u,u) = 1).
 // ------------------------------------------------------------------------------------------------
 __global__ void k_finalize(int32_t n, int32_t B, const int32_t *__restrict__ qnode, const int32_t *__restrict__ rho_slot,
-                           const float *__restrict__ MD0, int32_t p0, float *__restrict__ out) {
+                           const float *__restrict__ MD0, int32_t p0, const int32_t *__restrict__ ext2int,
+                           float *__restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int32_t q = blockIdx.y;
     if (i >= n) return;
     const int32_t sl = rho_slot[q];
-    float v = sl >= 0 ? MD0[i * p0 + sl] : 0.f;
+    float v = sl >= 0 ? MD0[(int64_t)ext2int[i] * p0 + sl] : 0.f;
     if ((int32_t)i == qnode[q]) v = 1.f;
     out[(int64_t)q * n + i] = v;
 }
 
 void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,
-                     int32_t p0, float *out, cudaStream_t s) {
+                     int32_t p0, const int32_t *ext2int, float *out, cudaStream_t s) {
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)B);
-    k_finalize<<<grid, 256, 0, s>>>(n, B, qnode, rho_slot, MD0, p0, out);
+    k_finalize<<<grid, 256, 0, s>>>(n, B, qnode, rho_slot, MD0, p0, ext2int, out);
+}
+
+__global__ void k_map_ids(int32_t *ids, int64_t count, const int32_t *__restrict__ map) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count && ids[i] >= 0) ids[i] = map[ids[i]];
+}
+
+void launch_map_ids(int32_t *ids, int64_t count, const int32_t *map, cudaStream_t s) {
+    if (count <= 0) return;
+    k_map_ids<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(ids, count, map);
 }
 
 }  // namespace ps

@@ -6,11 +6,12 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <shared_mutex>
 #include <new>
 #include <string>
 #include <vector>
 
-#include "internal.cuh"
+#include "engine.cuh"
 
 using namespace ps;
 
@@ -25,6 +26,8 @@ static probesim_status fail(probesim_status st, const std::string &msg) {
     g_last_error = msg;
     return st;
 }
+
+probesim_status ps::fail_status(probesim_status st, const std::string &msg) { return fail(st, msg); }
 
 #define PS_CUDA(expr)                                                                                  \
     do {                                                                                               \
@@ -41,84 +44,17 @@ static probesim_status fail(probesim_status st, const std::string &msg) {
         if (_s != PROBESIM_OK) return _s;             \
     } while (0)
 
-// ------------------------------------------------------------------------------------------------
-// device buffers that grow on demand and are freed with the graph
-// ------------------------------------------------------------------------------------------------
-struct DevBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-    cudaError_t ensure(size_t bytes) {
-        if (bytes <= cap && p) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        const size_t nb = std::max<size_t>(256, bytes + bytes / 8);
-        cudaError_t e = cudaMalloc(&p, nb);
-        if (e == cudaSuccess) cap = nb; else cudaGetLastError();
-        return e;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-    template <class T>
-    T *as() const { return static_cast<T *>(p); }
-};
-
-struct PinnedBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-    cudaError_t ensure(size_t bytes) {
-        if (bytes <= cap && p) return cudaSuccess;
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        cap = 0;
-        const size_t nb = std::max<size_t>(256, bytes + bytes / 8);
-        cudaError_t e = cudaMallocHost(&p, nb);
-        if (e == cudaSuccess) cap = nb; else cudaGetLastError();
-        return e;
-    }
-    void release() {
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        cap = 0;
-    }
-    template <class T>
-    T *as() const { return static_cast<T *>(p); }
-};
-
-struct probesim_graph {
-    std::mutex mu;
-    probesim_config cfg{};
-    uint32_t t_stop = 0;
-    int device = 0;
-    DeviceGraph dg;
-    // device arrays of the graph store
-    DevBuf in_off, in_col, out_off, out_col, w, piece_v, piece_beg, piece_len, split_v;
-    // host copy of the edge set as sorted keys (dst << 32 | src), used to apply update batches
-    std::vector<uint64_t> keys;
-    uint64_t epoch = 0;
-    // query workspace
-    DevBuf qbuf, walks, lens, ctr;
-    DevBuf t_key, t_node, t_parent, t_depth, t_query, t_weight, t_height, t_slot, t_gamma, t_G;
-    DevBuf counts, offs, node_list, slot_entry, nchild, child_off, child_list, ccur, rho_slot;
-    DevBuf md_a, md_b, dmat, out_stage;
-    DevBuf tk_hist, tk_state, tk_tie, tk_cid, tk_cval, tk_ids, tk_vals, tk_qk;
-    PinnedBuf pin_q;  // query arrays of one batch
-    PinnedBuf pin_s;  // counters and schedule offsets (fixed size, allocated at creation)
-    // profiling
-    int profiling = 0;
-    std::vector<cudaEvent_t> ev;
-    probesim_stats stats{};
-    size_t budget = 0;
-};
-
 static uint32_t threshold_stop(double c) { return (uint32_t)std::floor((1.0 - std::sqrt(c)) * 4294967296.0); }
+static uint32_t threshold_keep(double c) {
+    const double t = std::floor(std::sqrt(c) * 4294967296.0);
+    return t >= 4294967295.0 ? 4294967295u : (uint32_t)t;
+}
 
 static int64_t num_walks(double c, double eps, double delta, int64_t n) {
     return (int64_t)std::ceil(3.0 * c / (eps * eps) * std::log((double)n / delta));
 }
+
+int64_t ps::num_walks_for(const probesim_graph *g, double eps) { return num_walks(g->cfg.c, eps, g->cfg.delta, g->dg.n); }
 
 static bool is_device_ptr(const void *p) {
     if (!p) return false;
@@ -135,28 +71,42 @@ static bool is_device_ptr(const void *p) {
 // graph store
 // ------------------------------------------------------------------------------------------------
 
-// Builds in-CSR (rows by destination, sources ascending), out-CSR (rows by source, destinations
-// ascending), w[v] = sqrt(c)/|I(v)| and the pull pieces from the sorted unique keys, and uploads them.
+// Builds the device graph store from the sorted unique keys (dst << 32 | src, external ids) and uploads it.
+// Internally nodes are renumbered by descending out-degree (ties by external id): the pull kernel gathers
+// score rows of in-neighbours, which are mostly high-out-degree nodes, so their rows become contiguous and
+// stay cached.  I(v) keeps its external source-id order (walks pick the k-th entry of that order) but holds
+// internal ids; O(x) holds internal ids in ascending order; ext2int / int2ext map at the boundary.
 static probesim_status upload_graph(probesim_graph *g, int32_t n, cudaStream_t st) {
     const std::vector<uint64_t> &K = g->keys;
     const int64_t m = (int64_t)K.size();
+    std::vector<int64_t> outdeg_ext(n, 0), ext_in_off(n + 1, 0);
+    for (int64_t e = 0; e < m; ++e) {
+        ext_in_off[(K[e] >> 32) + 1]++;
+        outdeg_ext[K[e] & 0xffffffffu]++;
+    }
+    for (int32_t v = 0; v < n; ++v) ext_in_off[v + 1] += ext_in_off[v];
+    std::vector<int32_t> int2ext(n), ext2int(n);
+    for (int32_t v = 0; v < n; ++v) int2ext[v] = v;
+    std::stable_sort(int2ext.begin(), int2ext.end(),
+                     [&](int32_t a, int32_t b) { return outdeg_ext[a] > outdeg_ext[b]; });
+    for (int32_t i = 0; i < n; ++i) ext2int[int2ext[i]] = i;
+    g->h_ext2int = ext2int;
     std::vector<int64_t> in_off(n + 1, 0), out_off(n + 1, 0);
     std::vector<int32_t> in_col(std::max<int64_t>(1, m)), out_col(std::max<int64_t>(1, m));
-    for (int64_t e = 0; e < m; ++e) {
-        in_off[(K[e] >> 32) + 1]++;
-        out_off[(K[e] & 0xffffffffu) + 1]++;
-        in_col[e] = (int32_t)(K[e] & 0xffffffffu);
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t v = int2ext[i];
+        in_off[i + 1] = in_off[i] + (ext_in_off[v + 1] - ext_in_off[v]);
+        out_off[i + 1] = out_off[i] + outdeg_ext[v];
     }
-    for (int32_t v = 0; v < n; ++v) {
-        in_off[v + 1] += in_off[v];
-        out_off[v + 1] += out_off[v];
+    for (int32_t i = 0; i < n; ++i) {  // in-list of internal row i, in external source order
+        const int32_t v = int2ext[i];
+        int64_t pos = in_off[i];
+        for (int64_t e = ext_in_off[v]; e < ext_in_off[v + 1]; ++e) in_col[pos++] = ext2int[K[e] & 0xffffffffu];
     }
     {
         std::vector<int64_t> cur(out_off.begin(), out_off.end() - 1);
-        for (int64_t e = 0; e < m; ++e) {  // keys ascend by destination: each out-row fills in ascending order
-            const int32_t src = (int32_t)(K[e] & 0xffffffffu);
-            out_col[cur[src]++] = (int32_t)(K[e] >> 32);
-        }
+        for (int32_t i = 0; i < n; ++i)  // rows visited in internal order: out-rows fill in ascending internal id
+            for (int64_t e = in_off[i]; e < in_off[i + 1]; ++e) out_col[cur[in_col[e]]++] = i;
     }
     const float sc = (float)std::sqrt(g->cfg.c);
     std::vector<float> w(n);
@@ -207,6 +157,8 @@ static probesim_status upload_graph(probesim_graph *g, int32_t n, cudaStream_t s
     PS_CUDA(g->in_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m)));
     PS_CUDA(g->out_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m)));
     PS_CUDA(g->w.ensure(sizeof(float) * n));
+    PS_CUDA(g->ext2int.ensure(sizeof(int32_t) * n));
+    PS_CUDA(g->int2ext.ensure(sizeof(int32_t) * n));
     PS_CUDA(g->piece_v.ensure(sizeof(int32_t) * std::max<size_t>(1, pv.size())));
     PS_CUDA(g->piece_beg.ensure(sizeof(int64_t) * std::max<size_t>(1, pb.size())));
     PS_CUDA(g->piece_len.ensure(sizeof(int32_t) * std::max<size_t>(1, pl.size())));
@@ -218,6 +170,8 @@ static probesim_status upload_graph(probesim_graph *g, int32_t n, cudaStream_t s
         PS_CUDA(cudaMemcpyAsync(g->out_col.p, out_col.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
     }
     PS_CUDA(cudaMemcpyAsync(g->w.p, w.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(g->ext2int.p, ext2int.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(g->int2ext.p, int2ext.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
     PS_CUDA(cudaMemcpyAsync(g->piece_v.p, pv.data(), sizeof(int32_t) * pv.size(), cudaMemcpyHostToDevice, st));
     PS_CUDA(cudaMemcpyAsync(g->piece_beg.p, pb.data(), sizeof(int64_t) * pb.size(), cudaMemcpyHostToDevice, st));
     PS_CUDA(cudaMemcpyAsync(g->piece_len.p, pl.data(), sizeof(int32_t) * pl.size(), cudaMemcpyHostToDevice, st));
@@ -238,6 +192,8 @@ static probesim_status upload_graph(probesim_graph *g, int32_t n, cudaStream_t s
     d.piece_len = g->piece_len.as<int32_t>();
     d.n_split = (int32_t)split.size();
     d.split_v = g->split_v.as<int32_t>();
+    d.ext2int = g->ext2int.as<int32_t>();
+    d.int2ext = g->int2ext.as<int32_t>();
     return PROBESIM_OK;
 }
 
@@ -289,20 +245,20 @@ static probesim_status plan_batch(probesim_graph *g, const probesim_query *q, in
 }
 
 // Uploads the batch arrays; returns the device view.
-static probesim_status upload_batch(probesim_graph *g, const BatchPlan &P, QueryBatch &qb, cudaStream_t st) {
+static probesim_status upload_batch(Workspace *ws, const BatchPlan &P, QueryBatch &qb, cudaStream_t st) {
     const int32_t B = P.B;
     const size_t bytes = sizeof(int32_t) * (4 * (size_t)B + 1) + sizeof(float) * B + 64;
-    PS_CUDA(g->pin_q.ensure(bytes));
-    PS_CUDA(g->qbuf.ensure(bytes));
-    char *h = g->pin_q.as<char>();
+    PS_CUDA(ws->pin_q.ensure(bytes));
+    PS_CUDA(ws->qbuf.ensure(bytes));
+    char *h = ws->pin_q.as<char>();
     int32_t *hn = reinterpret_cast<int32_t *>(h);
     std::memcpy(hn, P.node.data(), sizeof(int32_t) * B);
     std::memcpy(hn + B, P.qid.data(), sizeof(uint32_t) * B);
     std::memcpy(hn + 2 * B, P.base.data(), sizeof(int32_t) * (B + 1));
     std::memcpy(hn + 3 * B + 1, P.k0.data(), sizeof(int32_t) * B);
     std::memcpy(hn + 4 * B + 1, P.inv_nr.data(), sizeof(float) * B);
-    PS_CUDA(cudaMemcpyAsync(g->qbuf.p, h, bytes, cudaMemcpyHostToDevice, st));
-    int32_t *d = g->qbuf.as<int32_t>();
+    PS_CUDA(cudaMemcpyAsync(ws->qbuf.p, h, bytes, cudaMemcpyHostToDevice, st));
+    int32_t *d = ws->qbuf.as<int32_t>();
     qb.B = B;
     qb.node = d;
     qb.qid = reinterpret_cast<const uint32_t *>(d + B);
@@ -319,23 +275,52 @@ static int64_t next_pow2(int64_t x) {
 }
 
 struct Timer {
-    probesim_graph *g;
+    Workspace *ws;
     cudaStream_t st;
     size_t used = 0;
     cudaEvent_t get() {
-        if (used == g->ev.size()) {
+        if (used == ws->ev.size()) {
             cudaEvent_t e;
             cudaEventCreate(&e);
-            g->ev.push_back(e);
+            ws->ev.push_back(e);
         }
-        return g->ev[used++];
+        return ws->ev[used++];
+    }
+};
+
+// Brackets groups of launches with events when profiling is on; times are summed per phase after the
+// batch's final synchronisation.
+struct PhaseTimer {
+    Timer *tm;
+    bool on;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    int cur = -1;
+    cudaEvent_t e0 = nullptr;
+    void begin(int phase) {
+        if (!on) return;
+        cur = phase;
+        e0 = tm->get();
+        cudaEventRecord(e0, tm->st);
+    }
+    void end() {
+        if (!on || cur < 0) return;
+        cudaEvent_t e1 = tm->get();
+        cudaEventRecord(e1, tm->st);
+        marks.push_back({cur, {e0, e1}});
+        cur = -1;
+    }
+    void collect(probesim_stats &st) {
+        for (auto &m : marks) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess) st.phase_ms[m.first] += ms;
+        }
     }
 };
 
 // Runs the query path for one batch into d_out ([B][n] on the device).  Returns PROBESIM_E_NOMEM with
 // *too_big set when the level buffers of this batch would exceed the workspace budget.
-static probesim_status run_batch(probesim_graph *g, const probesim_query *q, int32_t B, float *d_out, cudaStream_t st,
-                                 bool *too_big) {
+static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t B, float *d_out,
+                                 cudaStream_t st, bool *too_big) {
     *too_big = false;
     const DeviceGraph &dg = g->dg;
     const int32_t n = dg.n;
@@ -347,183 +332,337 @@ static probesim_status run_batch(probesim_graph *g, const probesim_query *q, int
         return PROBESIM_E_NOMEM;
     }
     QueryBatch qb;
-    PS_TRY(upload_batch(g, P, qb, st));
+    PS_TRY(upload_batch(ws, P, qb, st));
     int64_t launches = 0;
+    Timer tm{ws, st};
+    PhaseTimer ph{&tm, ws->profiling != 0};
     // 1. walks (Def. 3)
-    PS_CUDA(g->walks.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)P.W * L)));
-    PS_CUDA(g->lens.ensure(sizeof(int32_t) * std::max<int32_t>(1, P.W)));
-    PS_CUDA(g->ctr.ensure(sizeof(LaunchCounters)));
-    LaunchCounters *d_ctr = g->ctr.as<LaunchCounters>();
+    PS_CUDA(ws->walks.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)P.W * L)));
+    PS_CUDA(ws->lens.ensure(sizeof(int32_t) * std::max<int32_t>(1, P.W)));
+    PS_CUDA(ws->ctr.ensure(sizeof(LaunchCounters)));
+    LaunchCounters *d_ctr = ws->ctr.as<LaunchCounters>();
     PS_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(LaunchCounters), st));
-    launch_walks(dg, qb, P.W, L, g->t_stop, g->cfg.seed, g->walks.as<int32_t>(), g->lens.as<int32_t>(), false, d_ctr, st);
+    ph.begin(0);
+    launch_walks(dg, qb, P.W, L, g->t_stop, g->cfg.seed, ws->walks.as<int32_t>(), ws->lens.as<int32_t>(), false, d_ctr, st);
+    ph.end();
     ++launches;
-    LaunchCounters *h_ctr = g->pin_s.as<LaunchCounters>();
+    LaunchCounters *h_ctr = ws->pin_s.as<LaunchCounters>();
     PS_CUDA(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(LaunchCounters), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     const int64_t walk_nodes = (int64_t)h_ctr->walk_nodes;
-    g->stats.walks += P.W;
-    g->stats.walk_nodes += walk_nodes;
+    ws->stats.walks += P.W;
+    ws->stats.walk_nodes += walk_nodes;
     // 2. reverse-reachability tree (Alg. 4) in a hash table at load <= 1/2
     TrieTable t;
     t.cap = next_pow2(std::max<int64_t>(1024, 2 * (walk_nodes + B) + 64));
     const size_t cap = (size_t)t.cap;
-    PS_CUDA(g->t_key.ensure(8 * cap));
-    PS_CUDA(g->t_node.ensure(4 * cap));
-    PS_CUDA(g->t_parent.ensure(4 * cap));
-    PS_CUDA(g->t_depth.ensure(4 * cap));
-    PS_CUDA(g->t_query.ensure(4 * cap));
-    PS_CUDA(g->t_weight.ensure(4 * cap));
-    PS_CUDA(g->t_height.ensure(4 * cap));
-    PS_CUDA(g->t_slot.ensure(4 * cap));
-    PS_CUDA(g->t_gamma.ensure(4 * cap));
-    PS_CUDA(g->t_G.ensure(4 * cap));
-    t.key = g->t_key.as<unsigned long long>();
-    t.node = g->t_node.as<int32_t>();
-    t.parent = g->t_parent.as<int32_t>();
-    t.depth = g->t_depth.as<int32_t>();
-    t.query = g->t_query.as<int32_t>();
-    t.weight = g->t_weight.as<int32_t>();
-    t.height = g->t_height.as<int32_t>();
-    t.slot = g->t_slot.as<int32_t>();
-    t.gamma = g->t_gamma.as<float>();
-    t.G = g->t_G.as<float>();
+    PS_CUDA(ws->t_key.ensure(8 * cap));
+    PS_CUDA(ws->t_node.ensure(4 * cap));
+    PS_CUDA(ws->t_parent.ensure(4 * cap));
+    PS_CUDA(ws->t_depth.ensure(4 * cap));
+    PS_CUDA(ws->t_query.ensure(4 * cap));
+    PS_CUDA(ws->t_weight.ensure(4 * cap));
+    PS_CUDA(ws->t_height.ensure(4 * cap));
+    PS_CUDA(ws->t_slot.ensure(4 * cap));
+    PS_CUDA(ws->t_gamma.ensure(4 * cap));
+    PS_CUDA(ws->t_G.ensure(4 * cap));
+    t.key = ws->t_key.as<unsigned long long>();
+    t.node = ws->t_node.as<int32_t>();
+    t.parent = ws->t_parent.as<int32_t>();
+    t.depth = ws->t_depth.as<int32_t>();
+    t.query = ws->t_query.as<int32_t>();
+    t.weight = ws->t_weight.as<int32_t>();
+    t.height = ws->t_height.as<int32_t>();
+    t.slot = ws->t_slot.as<int32_t>();
+    t.gamma = ws->t_gamma.as<float>();
+    t.G = ws->t_G.as<float>();
+    ph.begin(1);
     PS_CUDA(cudaMemsetAsync(t.key, 0xFF, 8 * cap, st));
     PS_CUDA(cudaMemsetAsync(t.weight, 0, 4 * cap, st));
     PS_CUDA(cudaMemsetAsync(t.height, 0, 4 * cap, st));
     PS_CUDA(cudaMemsetAsync(t.G, 0, 4 * cap, st));
-    launch_trie_insert(dg, qb, P.W, L, g->walks.as<int32_t>(), g->lens.as<int32_t>(), t, d_ctr, st);
+    launch_trie_insert(dg, qb, P.W, L, ws->walks.as<int32_t>(), ws->lens.as<int32_t>(), t, d_ctr, st);
     ++launches;
-    // 3. level schedule: nodes and vector slots per depth
+    // 3. level schedule: nodes, dense columns (pulled) and push columns per depth
     const int32_t D1 = L + 2;
-    PS_CUDA(g->counts.ensure(sizeof(int32_t) * 4 * D1));
-    int32_t *d_ncount = g->counts.as<int32_t>(), *d_scount = d_ncount + D1, *d_ncur = d_ncount + 2 * D1;
-    PS_CUDA(cudaMemsetAsync(d_ncount, 0, sizeof(int32_t) * 3 * D1, st));
-    launch_sched_count(t, d_ncount, d_scount, st);
+    PS_CUDA(ws->counts.ensure(sizeof(int32_t) * 5 * D1));
+    int32_t *d_ncount = ws->counts.as<int32_t>(), *d_scount = d_ncount + D1, *d_hcount = d_ncount + 2 * D1,
+            *d_ncur = d_ncount + 3 * D1;
+    PS_CUDA(cudaMemsetAsync(d_ncount, 0, sizeof(int32_t) * 4 * D1, st));
+    launch_sched_count(t, d_ncount, d_scount, d_hcount, st);
+    ph.end();
     ++launches;
-    int32_t *h_cnt = reinterpret_cast<int32_t *>(g->pin_s.as<char>() + 256);
-    PS_CUDA(cudaMemcpyAsync(h_cnt, d_ncount, sizeof(int32_t) * 2 * D1, cudaMemcpyDeviceToHost, st));
+    int32_t *h_cnt = reinterpret_cast<int32_t *>(ws->pin_s.as<char>() + 256);
+    PS_CUDA(cudaMemcpyAsync(h_cnt, d_ncount, sizeof(int32_t) * 3 * D1, cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(LaunchCounters), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     if (h_ctr->overflow) return fail(PROBESIM_E_CUDA, "internal: walk tree table overflow");
-    std::vector<int32_t> ncount(h_cnt, h_cnt + D1), scount(h_cnt + D1, h_cnt + 2 * D1);
+    std::vector<int32_t> ncount(h_cnt, h_cnt + D1), scount(h_cnt + D1, h_cnt + 2 * D1),
+        hcount(h_cnt + 2 * D1, h_cnt + 3 * D1);
     int32_t Dmax = 0;
     for (int32_t d = 0; d < D1; ++d)
         if (ncount[d] > 0) Dmax = d;
-    std::vector<int32_t> node_off(D1 + 1, 0), slot_off(D1 + 1, 0), pitch(D1, 0), tile(D1, 1);
-    int64_t maxpitch = 1;
+    // per depth: tile of the pull, dense width dw (multiple of the tile), columns cols = dw + push columns,
+    // row pitch of MD (float4 rows when the tile is >= 4)
+    std::vector<int32_t> node_off(D1 + 1, 0), slot_off(D1 + 1, 0), pitch(D1, 0), tile(D1, 1), dw(D1, 0), cols(D1, 0);
+    int64_t maxpitch = 1, maxdw = 1;
     for (int32_t d = 0; d < D1; ++d) {
         node_off[d + 1] = node_off[d] + ncount[d];
-        slot_off[d + 1] = slot_off[d] + scount[d];
-        if (scount[d] > 0) {
-            tile[d] = pull_tile_for(scount[d]);
-            pitch[d] = round_up(scount[d], tile[d]);
-            maxpitch = std::max<int64_t>(maxpitch, pitch[d]);
-        }
+        tile[d] = pull_tile_for(std::max(1, scount[d]));
+        dw[d] = scount[d] > 0 ? round_up(scount[d], tile[d]) : 0;
+        cols[d] = dw[d] + hcount[d];
+        pitch[d] = cols[d] > 0 ? round_up(cols[d], std::min(4, tile[d])) : 0;  // rows aligned for the pull's vectors
+        slot_off[d + 1] = slot_off[d] + cols[d];
+        maxpitch = std::max<int64_t>(maxpitch, pitch[d]);
+        maxdw = std::max<int64_t>(maxdw, dw[d]);
     }
     const int32_t total_nodes = node_off[D1], S_total = slot_off[D1];
-    g->stats.tree_nodes += total_nodes;
-    g->stats.vectors += S_total;
-    const size_t level_bytes = 3 * (size_t)n * (size_t)maxpitch * sizeof(float);
+    ws->stats.tree_nodes += total_nodes;
+    for (int32_t d = 0; d < D1; ++d) ws->stats.vectors += scount[d] + hcount[d];
+    const size_t level_bytes = (2 * (size_t)maxpitch + (size_t)maxdw) * (size_t)n * sizeof(float);
     if (level_bytes > g->budget) {
         *too_big = B > 1;
         return fail(PROBESIM_E_NOMEM, "score vectors of one query exceed the workspace budget");
     }
-    PS_CUDA(g->offs.ensure(sizeof(int32_t) * 2 * (D1 + 1)));
-    int32_t *d_node_off = g->offs.as<int32_t>(), *d_slot_off = d_node_off + D1 + 1;
-    int32_t *h_offs = h_cnt + 2 * D1;
+    PS_CUDA(ws->offs.ensure(sizeof(int32_t) * 3 * (D1 + 1)));
+    int32_t *d_node_off = ws->offs.as<int32_t>(), *d_slot_off = d_node_off + D1 + 1, *d_dw = d_slot_off + D1 + 1;
+    int32_t *h_offs = h_cnt + 3 * D1;
     std::memcpy(h_offs, node_off.data(), sizeof(int32_t) * (D1 + 1));
     std::memcpy(h_offs + D1 + 1, slot_off.data(), sizeof(int32_t) * (D1 + 1));
-    PS_CUDA(cudaMemcpyAsync(d_node_off, h_offs, sizeof(int32_t) * 2 * (D1 + 1), cudaMemcpyHostToDevice, st));
-    PS_CUDA(g->node_list.ensure(sizeof(int32_t) * std::max(1, total_nodes)));
-    PS_CUDA(g->slot_entry.ensure(sizeof(int32_t) * std::max(1, S_total)));
-    PS_CUDA(g->nchild.ensure(sizeof(int32_t) * std::max(1, S_total)));
-    PS_CUDA(g->child_off.ensure(sizeof(int32_t) * (S_total + 1)));
-    PS_CUDA(g->child_list.ensure(sizeof(int32_t) * std::max(1, S_total)));
-    PS_CUDA(g->ccur.ensure(sizeof(int32_t) * std::max(1, S_total)));
-    PS_CUDA(g->rho_slot.ensure(sizeof(int32_t) * B));
-    PS_CUDA(cudaMemsetAsync(g->nchild.p, 0, sizeof(int32_t) * std::max(1, S_total), st));
-    PS_CUDA(cudaMemsetAsync(g->ccur.p, 0, sizeof(int32_t) * std::max(1, S_total), st));
-    PS_CUDA(cudaMemsetAsync(g->rho_slot.p, 0xFF, sizeof(int32_t) * B, st));
-    launch_sched_lists(t, d_node_off, d_slot_off, d_ncur, g->node_list.as<int32_t>(), g->slot_entry.as<int32_t>(),
-                       g->nchild.as<int32_t>(), g->rho_slot.as<int32_t>(), st);
-    launch_scan_exclusive(g->nchild.as<int32_t>(), g->child_off.as<int32_t>(), S_total, st);
-    launch_sched_children(t, g->slot_entry.as<int32_t>(), S_total, d_slot_off, g->child_off.as<int32_t>(),
-                          g->ccur.as<int32_t>(), g->child_list.as<int32_t>(), st);
+    std::memcpy(h_offs + 2 * (D1 + 1), dw.data(), sizeof(int32_t) * D1);
+    PS_CUDA(cudaMemcpyAsync(d_node_off, h_offs, sizeof(int32_t) * 3 * (D1 + 1), cudaMemcpyHostToDevice, st));
+    PS_CUDA(ws->node_list.ensure(sizeof(int32_t) * std::max(1, total_nodes)));
+    PS_CUDA(ws->slot_entry.ensure(sizeof(int32_t) * std::max(1, S_total)));
+    PS_CUDA(ws->nchild.ensure(sizeof(int32_t) * std::max(1, S_total)));
+    PS_CUDA(ws->child_off.ensure(sizeof(int32_t) * (S_total + 1)));
+    PS_CUDA(ws->child_list.ensure(sizeof(int32_t) * std::max(1, S_total)));
+    PS_CUDA(ws->ccur.ensure(sizeof(int32_t) * std::max(1, S_total)));
+    PS_CUDA(ws->rho_slot.ensure(sizeof(int32_t) * B));
+    ph.begin(1);
+    PS_CUDA(cudaMemsetAsync(ws->slot_entry.p, 0xFF, sizeof(int32_t) * std::max(1, S_total), st));
+    PS_CUDA(cudaMemsetAsync(ws->nchild.p, 0, sizeof(int32_t) * std::max(1, S_total), st));
+    PS_CUDA(cudaMemsetAsync(ws->ccur.p, 0, sizeof(int32_t) * std::max(1, S_total), st));
+    PS_CUDA(cudaMemsetAsync(ws->rho_slot.p, 0xFF, sizeof(int32_t) * B, st));
+    launch_sched_lists(t, d_node_off, d_slot_off, d_dw, d_ncur, ws->node_list.as<int32_t>(), ws->slot_entry.as<int32_t>(),
+                       ws->nchild.as<int32_t>(), ws->rho_slot.as<int32_t>(), st);
+    launch_scan_exclusive(ws->nchild.as<int32_t>(), ws->child_off.as<int32_t>(), S_total, st);
+    launch_sched_children(t, ws->slot_entry.as<int32_t>(), S_total, d_slot_off, ws->child_off.as<int32_t>(),
+                          ws->ccur.as<int32_t>(), ws->child_list.as<int32_t>(), st);
+    ph.end();
     launches += 3;
-    // 4. level loop, deepest depth first
-    const size_t vec_bytes = (size_t)n * (size_t)maxpitch * sizeof(float);
-    PS_CUDA(g->md_a.ensure(vec_bytes));
-    PS_CUDA(g->md_b.ensure(vec_bytes));
-    PS_CUDA(g->dmat.ensure(vec_bytes));
-    float *prev = g->md_a.as<float>(), *cur = g->md_b.as<float>(), *Dm = g->dmat.as<float>();
-    const int32_t *node_list = g->node_list.as<int32_t>();
-    Timer tm{g, st};
+    // 4. level loop, deepest depth first.  MD buffers are [n][pitch]; D is [n][dw] (dense columns only).
+    PS_CUDA(ws->md_a.ensure((size_t)n * (size_t)maxpitch * sizeof(float)));
+    PS_CUDA(ws->md_b.ensure((size_t)n * (size_t)maxpitch * sizeof(float)));
+    PS_CUDA(ws->dmat.ensure((size_t)n * (size_t)maxdw * sizeof(float)));
+    float *prev = ws->md_a.as<float>(), *cur = ws->md_b.as<float>(), *Dm = ws->dmat.as<float>();
+    const int32_t *node_list = ws->node_list.as<int32_t>();
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks;
     for (int32_t d = Dmax; d >= 0; --d) {
-        const int32_t S = scount[d], pd = pitch[d];
+        const int32_t S = scount[d], H = hcount[d], pd = pitch[d], wd = dw[d];
         if (S > 0) {
-            if (d + 1 <= Dmax && scount[d + 1] > 0) {
-                launch_dbuild(n, prev, pitch[d + 1], Dm, pd, S, g->child_off.as<int32_t>() + slot_off[d],
-                              g->child_list.as<int32_t>(), st);
+            ph.begin(2);
+            if (d + 1 <= Dmax && cols[d + 1] > 0) {
+                launch_dbuild(n, prev, pitch[d + 1], Dm, wd, S, ws->child_off.as<int32_t>() + slot_off[d],
+                              ws->child_list.as<int32_t>(), st);
                 ++launches;
             } else {
-                PS_CUDA(cudaMemsetAsync(Dm, 0, (size_t)n * pd * sizeof(float), st));
+                PS_CUDA(cudaMemsetAsync(Dm, 0, (size_t)n * wd * sizeof(float), st));
             }
+            ph.end();
             if (d + 2 <= Dmax) {
-                launch_scatter_gamma(node_list + node_off[d + 2], ncount[d + 2], t, Dm, pd, st);
+                ph.begin(3);
+                launch_scatter_gamma(node_list + node_off[d + 2], ncount[d + 2], t, Dm, wd, wd, st);
+                ph.end();
                 ++launches;
             }
             if (dg.n_split > 0) {
-                launch_zero_split_rows(dg, cur, pd, st);
+                ph.begin(4);
+                launch_zero_split_rows(dg, cur, pd, wd, st);
+                ph.end();
                 ++launches;
             }
             cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (g->profiling) {
+            if (ws->profiling) {
                 e0 = tm.get();
                 e1 = tm.get();
                 PS_CUDA(cudaEventRecord(e0, st));
             }
-            launch_pull(dg, Dm, cur, pd, tile[d], st);
+            launch_pull(dg, Dm, wd, cur, pd, tile[d], st);
             ++launches;
-            if (g->profiling) {
+            if (ws->profiling) {
                 PS_CUDA(cudaEventRecord(e1, st));
                 marks.push_back({e0, e1});
             }
-            g->stats.probe_launches += 1;
-            g->stats.edge_gathers += dg.m * (int64_t)S;
-            g->stats.probe_bytes += 4.0 * dg.m + 16.0 * dg.n_pieces + 4.0 * n + 8.0 * (double)n * S;
+            ws->stats.probe_launches += 1;
+            ws->stats.edge_gathers += dg.m * (int64_t)S;
+            ws->stats.probe_bytes += 4.0 * dg.m + 16.0 * dg.n_pieces + 4.0 * n + 8.0 * (double)n * S;
+        }
+        if (H > 0) {  // height-2 columns: zero, then push from the grandchildren's gamma
+            ph.begin(6);
+            launch_zero_cols(n, cur, pd, wd, H, st);
+            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, cur, pd, wd, st);
+            ph.end();
+            ++launches;
         }
         if (d >= 1) {
-            launch_gamma(dg, node_list + node_off[d], ncount[d], t, qb.inv_nr, S > 0 ? cur : nullptr, pd, st);
+            ph.begin(7);
+            launch_gamma(dg, node_list + node_off[d], ncount[d], t, qb.inv_nr, cols[d] > 0 ? cur : nullptr, pd, st);
+            ph.end();
             ++launches;
         }
         std::swap(prev, cur);
-        g->stats.levels += 1;
+        ws->stats.levels += 1;
     }
     // 5. estimates: s(u, v) = MD(super-root)[v], s(u, u) = 1
-    launch_finalize(n, B, qb.node, g->rho_slot.as<int32_t>(), scount[0] > 0 ? prev : nullptr, std::max(1, pitch[0]),
-                    d_out, st);
+    ph.begin(8);
+    launch_finalize(n, B, qb.node, ws->rho_slot.as<int32_t>(), cols[0] > 0 ? prev : nullptr, std::max(1, pitch[0]),
+                    dg.ext2int, d_out, st);
+    ph.end();
     ++launches;
     PS_CUDA(cudaGetLastError());
     PS_CUDA(cudaStreamSynchronize(st));
+    ph.collect(ws->stats);
     for (auto &mk : marks) {
         float ms = 0.f;
         PS_CUDA(cudaEventElapsedTime(&ms, mk.first, mk.second));
-        g->stats.probe_ms += ms;
+        ws->stats.probe_ms += ms;
+        ws->stats.phase_ms[5] += ms;
     }
-    g->stats.kernel_launches += launches;
+    ws->stats.kernel_launches += launches;
+    return PROBESIM_OK;
+}
+
+// Randomized PROBE (Alg. 3) for every probe of Alg. 1: one instance per (walk, prefix length), run level by
+// level over hash-set frontiers; the estimate is the member count of the final levels divided by n_r.
+static probesim_status run_batch_rand(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t B,
+                                      float *d_out, cudaStream_t st, bool *too_big) {
+    *too_big = false;
+    const DeviceGraph &dg = g->dg;
+    const int32_t n = dg.n, L = g->cfg.l_max;
+    BatchPlan P;
+    PS_TRY(plan_batch(g, q, B, P));
+    QueryBatch qb;
+    PS_TRY(upload_batch(ws, P, qb, st));
+    int64_t launches = 0;
+    const int32_t W = P.W;
+    PS_CUDA(ws->walks.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)W * L)));
+    PS_CUDA(ws->lens.ensure(sizeof(int32_t) * std::max<int32_t>(1, W)));
+    PS_CUDA(ws->ctr.ensure(sizeof(LaunchCounters)));
+    LaunchCounters *d_ctr = ws->ctr.as<LaunchCounters>();
+    PS_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(LaunchCounters), st));
+    launch_walks(dg, qb, W, L, g->t_stop, g->cfg.seed, ws->walks.as<int32_t>(), ws->lens.as<int32_t>(), false, d_ctr, st);
+    ++launches;
+    // instances: one per (walk, i), i = 2..len
+    PS_CUDA(ws->r_cnt.ensure(sizeof(long long) * std::max(1, W)));
+    PS_CUDA(ws->r_off.ensure(sizeof(long long) * (W + 1)));
+    PS_CUDA(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(W)));
+    launch_inst_count(ws->lens.as<int32_t>(), W, ws->r_cnt.as<long long>(), st);
+    launch_scan64(ws->r_cnt.as<long long>(), W, ws->r_part.as<long long>(), ws->r_off.as<long long>(), st);
+    launches += 4;
+    long long *h_ll = reinterpret_cast<long long *>(ws->pin_s.as<char>() + 32768);
+    LaunchCounters *h_ctr = ws->pin_s.as<LaunchCounters>();
+    PS_CUDA(cudaMemcpyAsync(h_ll, ws->r_off.as<long long>() + W, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(LaunchCounters), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    const int64_t NI = h_ll[0];
+    const int32_t max_len = h_ctr->max_len;
+    ws->stats.walks += W;
+    ws->stats.walk_nodes += (int64_t)h_ctr->walk_nodes;
+    if (NI >= ((int64_t)1 << 31)) return fail(PROBESIM_E_INVALID, "too many probe instances in one call");
+    PS_CUDA(ws->r_iwalk.ensure(sizeof(int32_t) * std::max<int64_t>(1, NI)));
+    PS_CUDA(ws->r_ilen.ensure(sizeof(int32_t) * std::max<int64_t>(1, NI)));
+    PS_CUDA(ws->r_iq.ensure(sizeof(int32_t) * std::max<int64_t>(1, NI)));
+    PS_CUDA(ws->r_ik.ensure(sizeof(uint32_t) * std::max<int64_t>(1, NI)));
+    PS_CUDA(ws->r_counts.ensure(sizeof(int32_t) * (size_t)B * n));
+    PS_CUDA(cudaMemsetAsync(ws->r_counts.p, 0, sizeof(int32_t) * (size_t)B * n, st));
+    PS_CUDA(ws->r_ctr.ensure(sizeof(unsigned long long) * 4));
+    unsigned long long *d_fc = ws->r_ctr.as<unsigned long long>();
+    int32_t *d_over = reinterpret_cast<int32_t *>(d_fc + 2);
+    int cur = 0;
+    int64_t cap = next_pow2(std::max<int64_t>(1024, 2 * NI));
+    int64_t fcap = std::max<int64_t>(1, NI);
+    PS_CUDA(ws->r_keys[cur].ensure(8 * (size_t)cap));
+    PS_CUDA(ws->r_fi[cur].ensure(4 * (size_t)fcap));
+    PS_CUDA(ws->r_fn[cur].ensure(4 * (size_t)fcap));
+    PS_CUDA(cudaMemsetAsync(ws->r_keys[cur].p, 0xFF, 8 * (size_t)cap, st));
+    PS_CUDA(cudaMemsetAsync(d_fc, 0, sizeof(unsigned long long) * 4, st));
+    launch_inst_init(qb, dg, ws->lens.as<int32_t>(), W, L, ws->walks.as<int32_t>(), ws->r_off.as<long long>(),
+                     ws->r_iwalk.as<int32_t>(), ws->r_ilen.as<int32_t>(), ws->r_iq.as<int32_t>(), ws->r_ik.as<uint32_t>(),
+                     ws->r_fi[cur].as<int32_t>(), ws->r_fn[cur].as<int32_t>(), d_fc, ws->r_keys[cur].as<unsigned long long>(),
+                     cap, d_over, st);
+    ++launches;
+    PS_CUDA(cudaMemcpyAsync(h_ll, d_fc, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    if (reinterpret_cast<int32_t *>(h_ll + 2)[0]) return fail(PROBESIM_E_CUDA, "internal: frontier set overflow");
+    int64_t F = (int64_t)((unsigned long long *)h_ll)[0];
+    int64_t cur_cap = cap;
+    for (int32_t j = 0; j + 2 <= max_len && F > 0; ++j) {
+        // out-degree prefix sums of the frontier
+        PS_CUDA(ws->r_deg.ensure(sizeof(long long) * F));
+        PS_CUDA(ws->r_pref.ensure(sizeof(long long) * (F + 1)));
+        PS_CUDA(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(F)));
+        launch_frontier_degree(ws->r_fi[cur].as<int32_t>(), ws->r_fn[cur].as<int32_t>(), F, ws->r_ilen.as<int32_t>(), j,
+                               dg.out_off, ws->r_deg.as<long long>(), st);
+        launch_scan64(ws->r_deg.as<long long>(), F, ws->r_part.as<long long>(), ws->r_pref.as<long long>(), st);
+        launches += 4;
+        PS_CUDA(cudaMemcpyAsync(h_ll, ws->r_pref.as<long long>() + F, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        const int64_t E = h_ll[0];
+        if (E <= 0) break;
+        const int nx = cur ^ 1;
+        const int64_t ncap = next_pow2(std::max<int64_t>(1024, 2 * E));
+        PS_CUDA(ws->r_keys[nx].ensure(8 * (size_t)ncap));
+        PS_CUDA(ws->r_fi[nx].ensure(4 * (size_t)E));
+        PS_CUDA(ws->r_fn[nx].ensure(4 * (size_t)E));
+        PS_CUDA(cudaMemsetAsync(ws->r_keys[nx].p, 0xFF, 8 * (size_t)ncap, st));
+        PS_CUDA(cudaMemsetAsync(d_fc, 0, sizeof(unsigned long long), st));
+        RandLevel Lv;
+        Lv.fr_inst = ws->r_fi[cur].as<int32_t>();
+        Lv.fr_node = ws->r_fn[cur].as<int32_t>();
+        Lv.F = F;
+        Lv.prefix = ws->r_pref.as<long long>();
+        Lv.E = E;
+        Lv.cur_keys = ws->r_keys[cur].as<unsigned long long>();
+        Lv.cur_cap = cur_cap;
+        Lv.next_keys = ws->r_keys[nx].as<unsigned long long>();
+        Lv.next_cap = ncap;
+        Lv.next_inst = ws->r_fi[nx].as<int32_t>();
+        Lv.next_node = ws->r_fn[nx].as<int32_t>();
+        Lv.next_count = d_fc;
+        Lv.counts = ws->r_counts.as<int32_t>();
+        Lv.overflow = d_over;
+        Lv.j = j;
+        launch_rand_level(dg, ws->walks.as<int32_t>(), L, ws->r_iwalk.as<int32_t>(), ws->r_ilen.as<int32_t>(),
+                          ws->r_iq.as<int32_t>(), ws->r_ik.as<uint32_t>(), qb.qid, g->cfg.seed, g->t_keep, Lv, st);
+        ++launches;
+        ws->stats.edge_gathers += E;
+        PS_CUDA(cudaMemcpyAsync(h_ll, d_fc, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        if (reinterpret_cast<int32_t *>(h_ll + 2)[0]) return fail(PROBESIM_E_CUDA, "internal: frontier set overflow");
+        F = (int64_t)((unsigned long long *)h_ll)[0];
+        cur = nx;
+        cur_cap = ncap;
+        ws->stats.levels += 1;
+    }
+    launch_rand_finalize(n, B, qb.node, ws->r_counts.as<int32_t>(), qb.inv_nr, dg.ext2int, d_out, st);
+    ++launches;
+    PS_CUDA(cudaGetLastError());
+    PS_CUDA(cudaStreamSynchronize(st));
+    ws->stats.kernel_launches += launches;
     return PROBESIM_OK;
 }
 
 // Runs all nq queries, splitting batches that do not fit the workspace budget.
-static probesim_status run_queries(probesim_graph *g, const probesim_query *q, int32_t nq, float *d_out,
+static probesim_status run_queries(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t nq, float *d_out,
                                    cudaStream_t st) {
     int32_t done = 0;
     int32_t chunk = nq;
     while (done < nq) {
         const int32_t B = std::min(chunk, nq - done);
         bool too_big = false;
-        probesim_status s = run_batch(g, q + done, B, d_out + (int64_t)done * g->dg.n, st, &too_big);
+        probesim_status s = g->cfg.probe_mode == PROBESIM_PROBE_RANDOMIZED
+                                ? run_batch_rand(g, ws, q + done, B, d_out + (int64_t)done * g->dg.n, st, &too_big)
+                                : run_batch(g, ws, q + done, B, d_out + (int64_t)done * g->dg.n, st, &too_big);
         if (s == PROBESIM_OK) {
             done += B;
             continue;
@@ -537,7 +676,7 @@ static probesim_status run_queries(probesim_graph *g, const probesim_query *q, i
     return PROBESIM_OK;
 }
 
-static probesim_status check_queries(const probesim_graph *g, const probesim_query *q, int32_t nq, bool topk,
+probesim_status ps::check_queries(const probesim_graph *g, const probesim_query *q, int32_t nq, bool topk,
                                      int32_t kmax) {
     if (!q || nq <= 0) return fail(PROBESIM_E_INVALID, "queries: null pointer or nq <= 0");
     if (nq > 65535) return fail(PROBESIM_E_INVALID, "at most 65535 queries per call");
@@ -583,8 +722,8 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
     if (c.l_max < 1 || c.l_max > 255) return fail(PROBESIM_E_INVALID, "l_max must lie in [1, 255]");
     if (!(c.eps_p >= 0.f) || !(c.c0 >= 0.f)) return fail(PROBESIM_E_INVALID, "eps_p and c0 must be >= 0");
     if (c.probe_mode < 0 || c.probe_mode > 2) return fail(PROBESIM_E_INVALID, "unknown probe_mode");
-    if (c.probe_mode != PROBESIM_PROBE_DETERMINISTIC || c.eps_p != 0.f)
-        return fail(PROBESIM_E_UNSUPPORTED, "this build runs the deterministic PROBE without Pruning Rule 2");
+    if (c.probe_mode == PROBESIM_PROBE_SWITCH || c.eps_p != 0.f)
+        return fail(PROBESIM_E_UNSUPPORTED, "this build runs the deterministic and randomized PROBE without Pruning Rule 2");
     std::vector<int32_t> hs, hd;
     PS_TRY(fetch_ids(src, m, hs));
     PS_TRY(fetch_ids(dst, m, hd));
@@ -594,11 +733,12 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
     if (!g) return fail(PROBESIM_E_NOMEM, "host allocation failed");
     g->cfg = c;
     g->t_stop = threshold_stop(c.c);
+    g->t_keep = threshold_keep(c.c);
     cudaGetDevice(&g->device);
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     g->budget = (size_t)(0.6 * (double)tot);
-    if (g->pin_s.ensure(65536) != cudaSuccess) {
+    if (g->ws0.pin_s.ensure(65536) != cudaSuccess) {
         delete g;
         return fail(PROBESIM_E_NOMEM, "pinned host allocation failed");
     }
@@ -612,6 +752,7 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
         probesim_graph_destroy(g);
         return s;
     }
+    std::vector<uint64_t>().swap(g->keys);  // later updates merge on the device
     *out = g;
     return PROBESIM_OK;
 }
@@ -619,16 +760,10 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
 probesim_status probesim_graph_destroy(probesim_graph *g) {
     if (!g) return PROBESIM_OK;
     DevBuf *bufs[] = {&g->in_off, &g->in_col, &g->out_off, &g->out_col, &g->w, &g->piece_v, &g->piece_beg,
-                      &g->piece_len, &g->split_v, &g->qbuf, &g->walks, &g->lens, &g->ctr, &g->t_key, &g->t_node,
-                      &g->t_parent, &g->t_depth, &g->t_query, &g->t_weight, &g->t_height, &g->t_slot, &g->t_gamma,
-                      &g->t_G, &g->counts, &g->offs, &g->node_list, &g->slot_entry, &g->nchild, &g->child_off,
-                      &g->child_list, &g->ccur, &g->rho_slot, &g->md_a, &g->md_b, &g->dmat, &g->out_stage,
-                      &g->tk_hist, &g->tk_state, &g->tk_tie, &g->tk_cid, &g->tk_cval, &g->tk_ids, &g->tk_vals,
-                      &g->tk_qk};
+                      &g->piece_len, &g->split_v, &g->ext2int, &g->int2ext, &g->u_batch, &g->u_valid,
+                      &g->u_vpre, &g->u_delta, &g->u_deg, &g->u_part, &g->u_hist};
     for (DevBuf *b : bufs) b->release();
-    g->pin_q.release();
-    g->pin_s.release();
-    for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+    g->ws0.release();
     delete g;
     return PROBESIM_OK;
 }
@@ -641,11 +776,13 @@ probesim_status probesim_graph_info(const probesim_graph *g, int32_t *n, int64_t
     return PROBESIM_OK;
 }
 
-static probesim_status apply_updates(probesim_graph *g, const int32_t *src, const int32_t *dst, int64_t k, bool insert,
-                                     int64_t *applied, cudaStream_t st) {
+}  // extern "C"
+
+probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const int32_t *dst, int64_t k, bool insert,
+                                  int64_t *applied, cudaStream_t st) {
     if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
     if (k < 0 || (k > 0 && (!src || !dst))) return fail(PROBESIM_E_INVALID, "bad update batch");
-    std::lock_guard<std::mutex> lk(g->mu);
+    std::unique_lock<std::shared_mutex> lk(g->store_mu);
     g_last_error.clear();
     std::vector<int32_t> hs, hd;
     PS_TRY(fetch_ids(src, k, hs));
@@ -653,34 +790,129 @@ static probesim_status apply_updates(probesim_graph *g, const int32_t *src, cons
     const int32_t n = g->dg.n;
     for (int64_t e = 0; e < k; ++e)
         if (hs[e] < 0 || hs[e] >= n || hd[e] < 0 || hd[e] >= n) return fail(PROBESIM_E_RANGE, "edge id outside [0, n)");
-    std::vector<uint64_t> batch;
-    batch.reserve(k);
-    for (int64_t e = 0; e < k; ++e)
-        if (hs[e] != hd[e]) batch.push_back(((uint64_t)(uint32_t)hd[e] << 32) | (uint32_t)hs[e]);
-    std::sort(batch.begin(), batch.end());
-    batch.erase(std::unique(batch.begin(), batch.end()), batch.end());
-    std::vector<uint64_t> next;
-    int64_t changed = 0;
-    if (insert) {
-        std::vector<uint64_t> fresh;
-        std::set_difference(batch.begin(), batch.end(), g->keys.begin(), g->keys.end(), std::back_inserter(fresh));
-        changed = (int64_t)fresh.size();
-        next.reserve(g->keys.size() + fresh.size());
-        std::merge(g->keys.begin(), g->keys.end(), fresh.begin(), fresh.end(), std::back_inserter(next));
-    } else {
-        next.reserve(g->keys.size());
-        std::set_difference(g->keys.begin(), g->keys.end(), batch.begin(), batch.end(), std::back_inserter(next));
-        changed = (int64_t)(g->keys.size() - next.size());
+    // the batch without loops and repeats, in the two row orders
+    std::vector<uint64_t> in_keys, out_keys;
+    in_keys.reserve(k);
+    for (int64_t e = 0; e < k; ++e) {
+        if (hs[e] == hd[e]) continue;
+        in_keys.push_back(((uint64_t)(uint32_t)g->h_ext2int[hd[e]] << 32) | (uint32_t)hs[e]);  // (dst int, src ext)
     }
-    if ((int64_t)next.size() >= ((int64_t)1 << 31)) return fail(PROBESIM_E_INVALID, "edge count would reach 2^31");
-    if (changed > 0) {
-        g->keys.swap(next);
-        PS_TRY(upload_graph(g, n, st));
+    std::sort(in_keys.begin(), in_keys.end());
+    in_keys.erase(std::unique(in_keys.begin(), in_keys.end()), in_keys.end());
+    const int64_t K = (int64_t)in_keys.size();
+    if (K == 0) {
+        g->epoch += 1;
+        if (applied) *applied = 0;
+        return PROBESIM_OK;
     }
+    out_keys.resize(K);
+    std::vector<int32_t> hb(5 * K);
+    int32_t *in_dst = hb.data(), *in_src = in_dst + K, *in_src_ext = in_src + K, *out_src = in_src_ext + K,
+            *out_dst = out_src + K;
+    for (int64_t e = 0; e < K; ++e) {
+        const int32_t d_int = (int32_t)(in_keys[e] >> 32), s_ext = (int32_t)(in_keys[e] & 0xffffffffu);
+        const int32_t s_int = g->h_ext2int[s_ext];
+        in_dst[e] = d_int;
+        in_src[e] = s_int;
+        in_src_ext[e] = s_ext;
+        out_keys[e] = ((uint64_t)(uint32_t)s_int << 32) | (uint32_t)d_int;
+    }
+    std::sort(out_keys.begin(), out_keys.end());
+    for (int64_t e = 0; e < K; ++e) {
+        out_src[e] = (int32_t)(out_keys[e] >> 32);
+        out_dst[e] = (int32_t)(out_keys[e] & 0xffffffffu);
+    }
+    DeviceGraph &dg = g->dg;
+    PS_CUDA(g->u_batch.ensure(sizeof(int32_t) * 5 * K));
+    PS_CUDA(g->u_valid.ensure(sizeof(long long) * 2 * K));
+    PS_CUDA(g->u_vpre.ensure(sizeof(long long) * 2 * (K + 1)));
+    PS_CUDA(g->u_delta.ensure(sizeof(long long) * 2 * (size_t)n));
+    PS_CUDA(g->u_deg.ensure(sizeof(long long) * 2 * ((size_t)n + 1)));
+    PS_CUDA(g->u_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(K, n))));
+    PS_CUDA(g->u_hist.ensure(sizeof(unsigned long long) * (2 * (kPiece + 1) + 2)));
+    PS_CUDA(cudaMemcpyAsync(g->u_batch.p, hb.data(), sizeof(int32_t) * 5 * K, cudaMemcpyHostToDevice, st));
+    int32_t *db = g->u_batch.as<int32_t>();
+    UpdateBatchArgs a;
+    a.k = K;
+    a.in_dst = db; a.in_src = db + K; a.in_src_ext = db + 2 * K; a.out_src = db + 3 * K; a.out_dst = db + 4 * K;
+    a.in_valid = g->u_valid.as<long long>();
+    a.out_valid = a.in_valid + K;
+    long long *in_vpre = g->u_vpre.as<long long>(), *out_vpre = in_vpre + (K + 1);
+    a.in_vpre = in_vpre;
+    a.out_vpre = out_vpre;
+    a.insert = insert;
+    long long *in_delta = g->u_delta.as<long long>(), *out_delta = in_delta + n;
+    PS_CUDA(cudaMemsetAsync(in_delta, 0, sizeof(long long) * 2 * (size_t)n, st));
+    launch_upd_mark(dg, a, in_delta, out_delta, st);
+    launch_scan64(a.in_valid, K, g->u_part.as<long long>(), in_vpre, st);
+    launch_scan64(a.out_valid, K, g->u_part.as<long long>(), out_vpre, st);
+    // new offsets
+    long long *deg = g->u_deg.as<long long>(), *deg_out = deg + (n + 1);
+    DevBuf n_in_off, n_out_off, n_in_col, n_out_col;
+    PS_CUDA(n_in_off.ensure(sizeof(int64_t) * ((size_t)n + 1)));
+    PS_CUDA(n_out_off.ensure(sizeof(int64_t) * ((size_t)n + 1)));
+    launch_upd_degrees(n, dg.in_off, in_delta, deg, st);
+    launch_scan64(deg, n, g->u_part.as<long long>(), n_in_off.as<long long>(), st);
+    launch_upd_degrees(n, dg.out_off, out_delta, deg_out, st);
+    launch_scan64(deg_out, n, g->u_part.as<long long>(), n_out_off.as<long long>(), st);
+    long long hm[3] = {0, 0, 0};
+    PS_CUDA(cudaMemcpyAsync(&hm[0], n_in_off.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(&hm[1], n_out_off.as<long long>() + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(&hm[2], in_vpre + K, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    const int64_t m2 = hm[0];
+    if (m2 != hm[1]) return fail(PROBESIM_E_CUDA, "internal: in- and out-lists disagree after the update");
+    if (m2 >= ((int64_t)1 << 31)) return fail(PROBESIM_E_INVALID, "edge count would reach 2^31");
+    PS_CUDA(n_in_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m2)));
+    PS_CUDA(n_out_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m2)));
+    launch_upd_rows(dg, a, true, n_in_off.as<long long>(), n_in_col.as<int32_t>(), st);
+    launch_upd_rows(dg, a, false, n_out_off.as<long long>(), n_out_col.as<int32_t>(), st);
+    // w and pieces of the new in-lists
+    const int64_t cap_pieces = (int64_t)n + m2 / kPiece + 1;
+    DevBuf n_pv, n_pb, n_pl, n_split;
+    PS_CUDA(n_pv.ensure(sizeof(int32_t) * cap_pieces));
+    PS_CUDA(n_pb.ensure(sizeof(int64_t) * cap_pieces));
+    PS_CUDA(n_pl.ensure(sizeof(int32_t) * cap_pieces));
+    PS_CUDA(n_split.ensure(sizeof(int32_t) * (size_t)n));
+    launch_upd_w(n, n_in_off.as<long long>(), (float)std::sqrt(g->cfg.c), dg.w, deg, st);
+    unsigned long long *hist = g->u_hist.as<unsigned long long>(), *cursor = hist + (kPiece + 1),
+                       *nsplit = cursor + (kPiece + 1);
+    launch_upd_pieces(n, n_in_off.as<long long>(), hist, cursor, n_split.as<int32_t>(), nsplit, n_pv.as<int32_t>(),
+                      n_pb.as<int64_t>(), n_pl.as<int32_t>(), st);
+    std::vector<unsigned long long> hh(kPiece + 2);
+    PS_CUDA(cudaMemcpyAsync(hh.data(), hist, sizeof(unsigned long long) * (kPiece + 1), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(hh.data() + kPiece + 1, nsplit, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaGetLastError());
+    PS_CUDA(cudaStreamSynchronize(st));
+    int64_t npieces = 0;
+    for (int len = 0; len <= kPiece; ++len) npieces += (int64_t)hh[len];
+    // swap in the new store
+    std::swap(g->in_off, n_in_off);
+    std::swap(g->out_off, n_out_off);
+    std::swap(g->in_col, n_in_col);
+    std::swap(g->out_col, n_out_col);
+    std::swap(g->piece_v, n_pv);
+    std::swap(g->piece_beg, n_pb);
+    std::swap(g->piece_len, n_pl);
+    std::swap(g->split_v, n_split);
+    for (DevBuf *b : {&n_in_off, &n_out_off, &n_in_col, &n_out_col, &n_pv, &n_pb, &n_pl, &n_split}) b->release();
+    dg.m = m2;
+    dg.in_off = g->in_off.as<int64_t>();
+    dg.out_off = g->out_off.as<int64_t>();
+    dg.in_col = g->in_col.as<int32_t>();
+    dg.out_col = g->out_col.as<int32_t>();
+    dg.n_pieces = npieces;
+    dg.piece_v = g->piece_v.as<int32_t>();
+    dg.piece_beg = g->piece_beg.as<int64_t>();
+    dg.piece_len = g->piece_len.as<int32_t>();
+    dg.n_split = (int32_t)hh[kPiece + 1];
+    dg.split_v = g->split_v.as<int32_t>();
     g->epoch += 1;
-    if (applied) *applied = changed;
+    if (applied) *applied = hm[2];
     return PROBESIM_OK;
 }
+
+extern "C" {
 
 probesim_status probesim_insert_edges(probesim_graph *g, const int32_t *src, const int32_t *dst, int64_t k,
                                       int64_t *applied, void *stream) {
@@ -704,22 +936,25 @@ probesim_status probesim_sample_walks(probesim_graph *g, const probesim_query *q
     if (!g || !nodes || !lens) return fail(PROBESIM_E_INVALID, "null argument");
     PS_TRY(check_queries(g, q, nq, false, 0));
     std::lock_guard<std::mutex> lk(g->mu);
+    std::shared_lock<std::shared_mutex> sl(g->store_mu);
     g_last_error.clear();
+    Workspace *ws = &g->ws0;
     cudaStream_t st = (cudaStream_t)stream;
     BatchPlan P;
     PS_TRY(plan_batch(g, q, nq, P));
     if (P.W > capacity) return fail(PROBESIM_E_INVALID, "walk buffer too small");
     QueryBatch qb;
-    PS_TRY(upload_batch(g, P, qb, st));
+    PS_TRY(upload_batch(ws, P, qb, st));
     const int32_t L = g->cfg.l_max;
     const bool dev_nodes = is_device_ptr(nodes), dev_lens = is_device_ptr(lens);
-    PS_CUDA(g->walks.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)P.W * L)));
-    PS_CUDA(g->lens.ensure(sizeof(int32_t) * std::max<int32_t>(1, P.W)));
-    PS_CUDA(g->ctr.ensure(sizeof(LaunchCounters)));
-    PS_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(LaunchCounters), st));
-    int32_t *wd = dev_nodes ? nodes : g->walks.as<int32_t>();
-    int32_t *ld = dev_lens ? lens : g->lens.as<int32_t>();
-    launch_walks(g->dg, qb, P.W, L, g->t_stop, g->cfg.seed, wd, ld, true, g->ctr.as<LaunchCounters>(), st);
+    PS_CUDA(ws->walks.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)P.W * L)));
+    PS_CUDA(ws->lens.ensure(sizeof(int32_t) * std::max<int32_t>(1, P.W)));
+    PS_CUDA(ws->ctr.ensure(sizeof(LaunchCounters)));
+    PS_CUDA(cudaMemsetAsync(ws->ctr.p, 0, sizeof(LaunchCounters), st));
+    int32_t *wd = dev_nodes ? nodes : ws->walks.as<int32_t>();
+    int32_t *ld = dev_lens ? lens : ws->lens.as<int32_t>();
+    launch_walks(g->dg, qb, P.W, L, g->t_stop, g->cfg.seed, wd, ld, true, ws->ctr.as<LaunchCounters>(), st);
+    ps::launch_map_ids(wd, (int64_t)P.W * L, g->dg.int2ext, st);
     PS_CUDA(cudaGetLastError());
     if (!dev_nodes)
         PS_CUDA(cudaMemcpyAsync(nodes, wd, sizeof(int32_t) * (size_t)P.W * L, cudaMemcpyDeviceToHost, st));
@@ -728,22 +963,21 @@ probesim_status probesim_sample_walks(probesim_graph *g, const probesim_query *q
     return PROBESIM_OK;
 }
 
-probesim_status probesim_single_source(probesim_graph *g, const probesim_query *q, int32_t nq, float *scores,
-                                       void *stream) {
-    if (!g || !scores) return fail(PROBESIM_E_INVALID, "null argument");
-    PS_TRY(check_queries(g, q, nq, false, 0));
-    std::lock_guard<std::mutex> lk(g->mu);
-    g_last_error.clear();
-    g->stats = probesim_stats{};
-    cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+// Single-source estimates of nq queries into `scores` (host or device) using workspace ws.  The caller holds
+// the store lock (shared) and owns ws.
+probesim_status ps::single_source_core(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t nq,
+                                          float *scores, cudaStream_t st) {
+    ws->stats = probesim_stats{};
     const bool dev = is_device_ptr(scores);
     float *d_out = scores;
     const size_t out_bytes = sizeof(float) * (size_t)nq * g->dg.n;
     if (!dev) {
-        PS_CUDA(g->out_stage.ensure(out_bytes));
-        d_out = g->out_stage.as<float>();
+        PS_CUDA(ws->out_stage.ensure(out_bytes));
+        d_out = ws->out_stage.as<float>();
     }
-    PS_TRY(run_queries(g, q, nq, d_out, st));
+    PS_TRY(run_queries(g, ws, q, nq, d_out, st));
     if (!dev) {
         PS_CUDA(cudaMemcpyAsync(scores, d_out, out_bytes, cudaMemcpyDeviceToHost, st));
         PS_CUDA(cudaStreamSynchronize(st));
@@ -751,49 +985,44 @@ probesim_status probesim_single_source(probesim_graph *g, const probesim_query *
     return PROBESIM_OK;
 }
 
-probesim_status probesim_topk(probesim_graph *g, const probesim_query *q, int32_t nq, int32_t kmax, int32_t *ids,
-                              float *vals, void *stream) {
-    if (!g || !ids || !vals) return fail(PROBESIM_E_INVALID, "null argument");
-    if (kmax < 1 || kmax > 4096 || kmax > g->dg.n - 1) return fail(PROBESIM_E_INVALID, "kmax must lie in [1, min(4096, n-1)]");
-    PS_TRY(check_queries(g, q, nq, true, kmax));
-    std::lock_guard<std::mutex> lk(g->mu);
-    g_last_error.clear();
-    g->stats = probesim_stats{};
-    cudaStream_t st = (cudaStream_t)stream;
+// Top-k of nq queries (ids/vals host or device, [nq][kmax]) using workspace ws; same locking as above.
+probesim_status ps::topk_core(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t nq, int32_t kmax,
+                                 int32_t *ids, float *vals, cudaStream_t st) {
+    ws->stats = probesim_stats{};
     const int32_t n = g->dg.n;
     // scores of a chunk of queries, then the selection
     const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(g->budget / 8) / ((int64_t)n * 4)));
-    PS_CUDA(g->out_stage.ensure(sizeof(float) * (size_t)chunk * n));
+    PS_CUDA(ws->out_stage.ensure(sizeof(float) * (size_t)chunk * n));
     const int nblk = topk_blocks_per_query(n);
-    PS_CUDA(g->tk_hist.ensure(sizeof(unsigned) * 256 * chunk));
-    PS_CUDA(g->tk_state.ensure(sizeof(unsigned) * 4 * chunk));
-    PS_CUDA(g->tk_tie.ensure(sizeof(unsigned) * (size_t)nblk * chunk));
-    PS_CUDA(g->tk_cid.ensure(sizeof(int32_t) * (size_t)kmax * chunk));
-    PS_CUDA(g->tk_cval.ensure(sizeof(float) * (size_t)kmax * chunk));
-    PS_CUDA(g->tk_qk.ensure(sizeof(int32_t) * 2 * chunk));
+    PS_CUDA(ws->tk_hist.ensure(sizeof(unsigned) * 256 * chunk));
+    PS_CUDA(ws->tk_state.ensure(sizeof(unsigned) * 4 * chunk));
+    PS_CUDA(ws->tk_tie.ensure(sizeof(unsigned) * (size_t)nblk * chunk));
+    PS_CUDA(ws->tk_cid.ensure(sizeof(int32_t) * (size_t)kmax * chunk));
+    PS_CUDA(ws->tk_cval.ensure(sizeof(float) * (size_t)kmax * chunk));
+    PS_CUDA(ws->tk_qk.ensure(sizeof(int32_t) * 2 * chunk));
     const bool dev_ids = is_device_ptr(ids), dev_vals = is_device_ptr(vals);
-    if (!dev_ids) PS_CUDA(g->tk_ids.ensure(sizeof(int32_t) * (size_t)kmax * chunk));
-    if (!dev_vals) PS_CUDA(g->tk_vals.ensure(sizeof(float) * (size_t)kmax * chunk));
+    if (!dev_ids) PS_CUDA(ws->tk_ids.ensure(sizeof(int32_t) * (size_t)kmax * chunk));
+    if (!dev_vals) PS_CUDA(ws->tk_vals.ensure(sizeof(float) * (size_t)kmax * chunk));
     std::vector<int32_t> hq(2 * chunk);
     for (int32_t done = 0; done < nq; done += chunk) {
         const int32_t B = std::min(chunk, nq - done);
-        PS_TRY(run_queries(g, q + done, B, g->out_stage.as<float>(), st));
+        PS_TRY(run_queries(g, ws, q + done, B, ws->out_stage.as<float>(), st));
         for (int32_t b = 0; b < B; ++b) {
             hq[b] = q[done + b].node;
             hq[chunk + b] = q[done + b].k;
         }
-        int32_t *d_qn = g->tk_qk.as<int32_t>(), *d_qk = d_qn + chunk;
+        int32_t *d_qn = ws->tk_qk.as<int32_t>(), *d_qk = d_qn + chunk;
         PS_CUDA(cudaMemcpyAsync(d_qn, hq.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, st));
         PS_CUDA(cudaMemcpyAsync(d_qk, hq.data() + chunk, sizeof(int32_t) * B, cudaMemcpyHostToDevice, st));
         TopkScratch sc;
-        sc.hist = g->tk_hist.as<unsigned>();
-        sc.state = g->tk_state.as<unsigned>();
-        sc.tiecnt = g->tk_tie.as<unsigned>();
-        sc.cand_id = g->tk_cid.as<int32_t>();
-        sc.cand_val = g->tk_cval.as<float>();
-        int32_t *oi = dev_ids ? ids + (int64_t)done * kmax : g->tk_ids.as<int32_t>();
-        float *ov = dev_vals ? vals + (int64_t)done * kmax : g->tk_vals.as<float>();
-        launch_topk(n, B, g->out_stage.as<float>(), d_qn, d_qk, kmax, sc, oi, ov, st, &g->stats.kernel_launches);
+        sc.hist = ws->tk_hist.as<unsigned>();
+        sc.state = ws->tk_state.as<unsigned>();
+        sc.tiecnt = ws->tk_tie.as<unsigned>();
+        sc.cand_id = ws->tk_cid.as<int32_t>();
+        sc.cand_val = ws->tk_cval.as<float>();
+        int32_t *oi = dev_ids ? ids + (int64_t)done * kmax : ws->tk_ids.as<int32_t>();
+        float *ov = dev_vals ? vals + (int64_t)done * kmax : ws->tk_vals.as<float>();
+        launch_topk(n, B, ws->out_stage.as<float>(), d_qn, d_qk, kmax, sc, oi, ov, st, &ws->stats.kernel_launches);
         PS_CUDA(cudaGetLastError());
         if (!dev_ids)
             PS_CUDA(cudaMemcpyAsync(ids + (int64_t)done * kmax, oi, sizeof(int32_t) * (size_t)B * kmax,
@@ -806,16 +1035,39 @@ probesim_status probesim_topk(probesim_graph *g, const probesim_query *q, int32_
     return PROBESIM_OK;
 }
 
+extern "C" {
+
+probesim_status probesim_single_source(probesim_graph *g, const probesim_query *q, int32_t nq, float *scores,
+                                       void *stream) {
+    if (!g || !scores) return fail(PROBESIM_E_INVALID, "null argument");
+    PS_TRY(check_queries(g, q, nq, false, 0));
+    std::lock_guard<std::mutex> lk(g->mu);
+    std::shared_lock<std::shared_mutex> sl(g->store_mu);
+    g_last_error.clear();
+    return single_source_core(g, &g->ws0, q, nq, scores, (cudaStream_t)stream);
+}
+
+probesim_status probesim_topk(probesim_graph *g, const probesim_query *q, int32_t nq, int32_t kmax, int32_t *ids,
+                              float *vals, void *stream) {
+    if (!g || !ids || !vals) return fail(PROBESIM_E_INVALID, "null argument");
+    if (kmax < 1 || kmax > 4096 || kmax > g->dg.n - 1) return fail(PROBESIM_E_INVALID, "kmax must lie in [1, min(4096, n-1)]");
+    PS_TRY(check_queries(g, q, nq, true, kmax));
+    std::lock_guard<std::mutex> lk(g->mu);
+    std::shared_lock<std::shared_mutex> sl(g->store_mu);
+    g_last_error.clear();
+    return topk_core(g, &g->ws0, q, nq, kmax, ids, vals, (cudaStream_t)stream);
+}
+
 probesim_status probesim_set_profiling(probesim_graph *g, int32_t on) {
     if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
     std::lock_guard<std::mutex> lk(g->mu);
-    g->profiling = on ? 1 : 0;
+    g->ws0.profiling = on ? 1 : 0;
     return PROBESIM_OK;
 }
 
 probesim_status probesim_get_stats(const probesim_graph *g, probesim_stats *out) {
     if (!g || !out) return fail(PROBESIM_E_INVALID, "null argument");
-    *out = g->stats;
+    *out = g->ws0.stats;
     return PROBESIM_OK;
 }
 

@@ -14,11 +14,11 @@ __device__ __forceinline__ int32_t query_of(const int32_t *walk_base, int32_t B,
     return lo;
 }
 
-// One thread per walk.  At node v: stop when the draw x0 is below t_stop (probability 1 - sqrt(c)),
+// One thread per walk, in internal node ids.  At node v: stop when the draw x0 is below t_stop (probability 1 - sqrt(c)),
 // stop when |I(v)| = 0, stop when the walk already holds l_max nodes; otherwise move to entry
 // floor(x1 * |I(v)| / 2^32) of I(v).
 __global__ void __launch_bounds__(256) k_walks(const int64_t *__restrict__ in_off, const int32_t *__restrict__ in_col,
-                                               QueryBatch q, int32_t W, int32_t l_max, uint32_t t_stop,
+                                               const int32_t *__restrict__ ext2int, QueryBatch q, int32_t W, int32_t l_max, uint32_t t_stop,
                                                uint32_t seed, int32_t *__restrict__ walks,
                                                int32_t *__restrict__ lens, bool pad, LaunchCounters *ctr) {
     const int32_t wid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) k_walks(const int64_t *__restrict__ in_of
         const int32_t b = query_of(q.walk_base, q.B, wid);
         const uint32_t k = (uint32_t)(q.walk_k0[b] + (wid - q.walk_base[b]));
         const uint32_t key1 = q.qid[b];
-        int32_t v = q.node[b];
+        int32_t v = ext2int[q.node[b]];
         int32_t *row = walks + (int64_t)wid * l_max;
         row[len++] = v;
         for (uint32_t s = 0;; ++s) {
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_walks(const int64_t *__restrict__ in_of
 void launch_walks(const DeviceGraph &g, const QueryBatch &q, int32_t W, int32_t l_max, uint32_t t_stop,
                   uint32_t seed, int32_t *walks, int32_t *lens, bool pad, LaunchCounters *ctr, cudaStream_t s) {
     if (W <= 0) return;
-    k_walks<<<(W + 255) / 256, 256, 0, s>>>(g.in_off, g.in_col, q, W, l_max, t_stop, seed, walks, lens, pad, ctr);
+    k_walks<<<(W + 255) / 256, 256, 0, s>>>(g.in_off, g.in_col, g.ext2int, q, W, l_max, t_stop, seed, walks, lens, pad, ctr);
 }
 
 // splitmix64 finalizer as the table hash
@@ -133,41 +133,55 @@ void launch_trie_insert(const DeviceGraph &g, const QueryBatch &q, int32_t W, in
     k_trie_insert<<<(W + 255) / 256, 256, 0, s>>>(q, W, l_max, walks, lens, t, ctr);
 }
 
-// Counts tree nodes and vector slots per depth.  A node gets a score vector (a slot) when its subtree has
+// Counts tree nodes and vector columns per depth.  A node owns a score-vector column when its subtree has
 // height >= 2: only then is the sum of its children's contributions more than a sparse set of nodes.
-__global__ void k_sched_count(TrieTable t, int32_t *ncount, int32_t *scount) {
+// Height >= 3 nodes (and a super-root of height 2) get "dense" columns filled by the pull; height-2 nodes
+// get "push" columns filled from their grandchildren's few gamma terms.  Dense columns take local indices
+// 0.., push columns are encoded -2 - local until the host knows the dense width of the depth.
+__global__ void k_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, int32_t *hcount) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= t.cap) return;
     if (t.key[e] == kEmptyKey) return;
-    const int32_t d = t.depth[e];
+    const int32_t d = t.depth[e], h = t.height[e];
     atomicAdd(&ncount[d], 1);
-    t.slot[e] = t.height[e] >= 2 ? atomicAdd(&scount[d], 1) : -1;
+    if (h >= 3 || (d == 0 && h >= 2)) t.slot[e] = atomicAdd(&scount[d], 1);
+    else if (h == 2) t.slot[e] = -2 - atomicAdd(&hcount[d], 1);
+    else t.slot[e] = -1;
 }
 
-void launch_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, cudaStream_t s) {
-    k_sched_count<<<(unsigned)((t.cap + 255) / 256), 256, 0, s>>>(t, ncount, scount);
+void launch_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, int32_t *hcount, cudaStream_t s) {
+    k_sched_count<<<(unsigned)((t.cap + 255) / 256), 256, 0, s>>>(t, ncount, scount, hcount);
 }
 
+// Node lists per depth, push columns placed after the dense width dw[d], the column -> tree-node map, the
+// child counts of every column (a column's parent always has a dense column), and each query's super-root.
 __global__ void k_sched_lists(TrieTable t, const int32_t *__restrict__ node_off, const int32_t *__restrict__ slot_off,
-                              int32_t *ncur, int32_t *node_list, int32_t *slot_entry, int32_t *nchild,
-                              int32_t *rho_slot) {
+                              const int32_t *__restrict__ dw, int32_t *ncur, int32_t *node_list, int32_t *slot_entry,
+                              int32_t *nchild, int32_t *rho_slot) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= t.cap) return;
     if (t.key[e] == kEmptyKey) return;
     const int32_t d = t.depth[e];
     node_list[node_off[d] + atomicAdd(&ncur[d], 1)] = (int32_t)e;
-    const int32_t sl = t.slot[e];
+    int32_t sl = t.slot[e];
+    if (sl <= -2) {
+        sl = dw[d] + (-2 - sl);
+        t.slot[e] = sl;
+    }
     if (sl >= 0) {
         slot_entry[slot_off[d] + sl] = (int32_t)e;
         const int32_t p = t.parent[e];
-        if (p >= 0) atomicAdd(&nchild[slot_off[d - 1] + t.slot[p]], 1);  // the parent's height is larger
+        if (p >= 0) {
+            int32_t ps = t.slot[p];  // dense (>= 0) by height; read before any rewrite could matter
+            atomicAdd(&nchild[slot_off[d - 1] + ps], 1);
+        }
     }
     if (d == 0) rho_slot[t.query[e]] = sl;
 }
 
-void launch_sched_lists(TrieTable t, const int32_t *node_off, const int32_t *slot_off, int32_t *ncur,
+void launch_sched_lists(TrieTable t, const int32_t *node_off, const int32_t *slot_off, const int32_t *dw, int32_t *ncur,
                         int32_t *node_list, int32_t *slot_entry, int32_t *nchild, int32_t *rho_slot, cudaStream_t s) {
-    k_sched_lists<<<(unsigned)((t.cap + 255) / 256), 256, 0, s>>>(t, node_off, slot_off, ncur, node_list, slot_entry,
+    k_sched_lists<<<(unsigned)((t.cap + 255) / 256), 256, 0, s>>>(t, node_off, slot_off, dw, ncur, node_list, slot_entry,
                                                                  nchild, rho_slot);
 }
 
@@ -206,6 +220,7 @@ __global__ void k_sched_children(TrieTable t, const int32_t *__restrict__ slot_e
     const int32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= S_total) return;
     const int32_t e = slot_entry[gid];
+    if (e < 0) return;  // padding column
     const int32_t p = t.parent[e];
     if (p < 0) return;
     const int32_t d = t.depth[e];

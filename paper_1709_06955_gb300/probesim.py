@@ -19,7 +19,9 @@ EXPORTS = [
     "probesim_config_default", "probesim_graph_create", "probesim_graph_destroy", "probesim_graph_info",
     "probesim_insert_edges", "probesim_delete_edges", "probesim_num_walks", "probesim_sample_walks",
     "probesim_single_source", "probesim_topk", "probesim_set_profiling", "probesim_get_stats",
-    "probesim_last_error", "probesim_topk_select_noalloc",
+    "probesim_last_error", "probesim_topk_select_noalloc", "probesim_server_config_default",
+    "probesim_server_create", "probesim_server_submit", "probesim_server_update", "probesim_server_poll",
+    "probesim_server_get_stats", "probesim_server_destroy",
 ]
 
 
@@ -36,7 +38,32 @@ class Query(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("walks", C.c_int64), ("walk_nodes", C.c_int64), ("tree_nodes", C.c_int64), ("vectors", C.c_int64),
                 ("levels", C.c_int64), ("edge_gathers", C.c_int64), ("probe_launches", C.c_int64),
-                ("probe_ms", C.c_double), ("probe_bytes", C.c_double), ("kernel_launches", C.c_int64)]
+                ("probe_ms", C.c_double), ("probe_bytes", C.c_double), ("kernel_launches", C.c_int64),
+                ("phase_ms", C.c_double * 12)]
+
+    PHASES = ["walks", "tree", "dbuild", "scatter", "zero_rows", "pull", "push", "gamma", "estimates"]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
+        d["phase_ms"] = {name: self.phase_ms[i] for i, name in enumerate(self.PHASES)}
+        return d
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("max_batch", C.c_int32), ("kmax", C.c_int32), ("queue_capacity", C.c_int32),
+                ("memory_budget_bytes", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("query_id", C.c_uint32), ("node", C.c_int32), ("k", C.c_int32),
+                ("status", C.c_int32), ("epoch", C.c_uint64), ("batch_size", C.c_int32), ("worker", C.c_int32),
+                ("queue_ms", C.c_double), ("latency_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64), ("failed", C.c_int64),
+                ("batches", C.c_int64), ("updates_applied", C.c_int64), ("mean_batch", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("qps", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +103,13 @@ def load(path=None):
     L.probesim_set_profiling.argtypes = [vp, C.c_int32]
     L.probesim_get_stats.argtypes = [vp, P(Stats)]
     L.probesim_topk_select_noalloc.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp, vp]
+    L.probesim_server_config_default.argtypes = [P(ServerConfig)]
+    L.probesim_server_create.argtypes = [vp, P(ServerConfig), P(vp)]
+    L.probesim_server_submit.argtypes = [vp, P(Query), C.c_int32, P(C.c_uint64)]
+    L.probesim_server_update.argtypes = [vp, vp, vp, C.c_int64, C.c_int32]
+    L.probesim_server_poll.argtypes = [vp, C.c_int32, C.c_int32, P(Result), vp, vp, P(C.c_int32), C.c_int32]
+    L.probesim_server_get_stats.argtypes = [vp, P(ServerStats)]
+    L.probesim_server_destroy.argtypes = [vp]
     for name in EXPORTS:
         if name != "probesim_last_error":
             getattr(L, name).restype = C.c_int
@@ -248,3 +282,54 @@ class Graph:
         s = Stats()
         _check(load().probesim_get_stats(self._h, C.byref(s)))
         return s.as_dict()
+
+
+class Server:
+    """Continuous-batching top-k server over a Graph (probesim_server_*)."""
+
+    def __init__(self, graph, workers=2, max_batch=16, kmax=100, queue_capacity=100000, memory_budget_bytes=0.0):
+        L = load()
+        cfg = ServerConfig()
+        _check(L.probesim_server_config_default(C.byref(cfg)))
+        cfg.workers, cfg.max_batch, cfg.kmax = int(workers), int(max_batch), int(kmax)
+        cfg.queue_capacity, cfg.memory_budget_bytes = int(queue_capacity), float(memory_budget_bytes)
+        h = C.c_void_p()
+        _check(L.probesim_server_create(graph._h, C.byref(cfg), C.byref(h)))
+        self._h = h
+        self.graph = graph
+        self.kmax = int(kmax)
+
+    def submit(self, queries):
+        t = (C.c_uint64 * len(queries))()
+        _check(load().probesim_server_submit(self._h, queries, len(queries), t))
+        return list(t)
+
+    def update(self, src, dst, insert=True):
+        src, dst = _int32(src), _int32(dst)
+        _check(load().probesim_server_update(self._h, _ptr(src), _ptr(dst), int(src.size), 1 if insert else 0))
+
+    def poll(self, max_results=64, wait_ms=100):
+        """Finished results: a list of (Result, ids[kmax], vals[kmax])."""
+        res = (Result * max_results)()
+        ids = np.zeros((max_results, self.kmax), np.int32)
+        vals = np.zeros((max_results, self.kmax), np.float32)
+        cnt = C.c_int32()
+        _check(load().probesim_server_poll(self._h, max_results, self.kmax, res, _ptr(ids), _ptr(vals), C.byref(cnt),
+                                           int(wait_ms)))
+        return [(res[i], ids[i].copy(), vals[i].copy()) for i in range(cnt.value)]
+
+    def stats(self):
+        st = ServerStats()
+        _check(load().probesim_server_get_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().probesim_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 -- interpreter shutdown
+            pass

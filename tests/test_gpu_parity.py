@@ -196,6 +196,42 @@ def test_updates_match_oracle(cfg1):
         out = G.single_source(_q([u], eps=0.15, query_ids=[t]))[0]
         ref, _ = O.single_source(int(u), eps=0.15, seed=3, qid=t)
         assert np.max(np.abs(out - ref)) <= TOL
+        nodes, lens = G.sample_walks(_q([u], eps=0.15, query_ids=[t]))  # in-lists keep the source-id order
+        for k in range(0, nodes.shape[0], 37):
+            w = O.walk(int(u), 0.6, 64, 3, t, k)
+            assert lens[k] == w.size and np.array_equal(nodes[k, :w.size], w)
+
+
+def test_updates_on_a_hub_row():
+    """One batch of many inserts into the in- and out-lists of a hub, then many deletes from its in-list."""
+    n = 3000
+    s, d = synth.chung_lu(n, 30000, seed=4)
+    hub = int(np.argmax(np.bincount(d, minlength=n)))
+    rng = np.random.default_rng(5)
+    in_src = rng.choice(n, 1500, replace=False).astype(np.int32)
+    out_dst = rng.choice(n, 700, replace=False).astype(np.int32)
+    add_s = np.concatenate([in_src, np.full(700, hub, np.int32)])
+    add_d = np.concatenate([np.full(1500, hub, np.int32), out_dst])
+    G = gpu_graph(n, s, d)
+    before = G.info()[1]
+    added = G.insert_edges(add_s, add_d)
+    cur_s, cur_d = dedup(n, np.concatenate([s, add_s]), np.concatenate([d, add_d]))
+    assert added == cur_s.size - before and G.info()[1] == cur_s.size
+    drop = rng.choice(np.nonzero(cur_d == hub)[0], 400, replace=False)
+    assert G.delete_edges(cur_s[drop], cur_d[drop]) == 400
+    keep = np.ones(cur_s.size, bool)
+    keep[drop] = False
+    cur_s, cur_d = cur_s[keep], cur_d[keep]
+    assert G.info()[1] == cur_s.size
+    O = oracle_graph(n, cur_s, cur_d)
+    for t, u in enumerate([hub] + list(synth.queries(n, cur_d, 2, seed=6))):
+        out = G.single_source(_q([u], eps=0.2, query_ids=[t]))[0]
+        ref, _ = O.single_source(int(u), eps=0.2, seed=3, qid=t)
+        assert np.max(np.abs(out - ref)) <= TOL
+        nodes, lens = G.sample_walks(_q([u], eps=0.2, query_ids=[t]))
+        for k in range(0, nodes.shape[0], 11):
+            w = O.walk(int(u), 0.6, 64, 3, t, k)
+            assert lens[k] == w.size and np.array_equal(nodes[k, :w.size], w)
 
 
 def test_errors(cfg1):
