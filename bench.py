@@ -223,6 +223,7 @@ def run_ours(args):
     build.build()
     n, s, d, qs = load_workload(args.workload)
     G = probesim.Graph(n, s, d)
+    tuning = G.autotune()  # launch shape of the pull kernel, chosen on this graph before timing
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     nq = len(qs)
@@ -295,6 +296,21 @@ def run_ours(args):
     bms = sum(a.elapsed_time(b) for a, b in bev)
     batched_qps = nb * B / (bms / 1e3)
 
+    # randomized PROBE (Alg. 3) on the same graph: a few queries one at a time
+    GR = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_RANDOMIZED)
+    rq = 5
+    GR.single_source(query(0), out=out, stream=sptr)
+    barrier()
+    r0 = time.perf_counter()
+    for i in range(rq):
+        GR.single_source(query(args.warmup + i), out=out, stream=sptr)
+    barrier()
+    rand_s = time.perf_counter() - r0
+    rstats = GR.stats()
+    GR.close()
+    randomized = {"value": rq / rand_s, "unit": "queries/s", "queries": rq,
+                  "candidates_per_query": rstats["edge_gathers"], "levels_per_query": rstats["levels"]}
+
     # serving leg: Poisson arrivals into the continuous-batching server (top-k, k in {10, 50, 100})
     serving = serving_leg(probesim, G, qs, args.serve_rate, args.serve_seconds, rank)
 
@@ -338,6 +354,7 @@ def run_ours(args):
             "config": {"workload": "R-MAT (.57,.19,.19,.05) n=2^20 m=2^24 seed 1, eps=0.1 delta=0.01 c=0.6 "
                                    "(n_r=3325), deterministic PROBE, one query per call",
                        "queries": "uniform over nodes with in-degree >= 1", "l2": "flushed between steps (256 MB write)",
+                       "pull_tuning": tuning,
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "p50_ms": pct(50), "p99_ms": pct(99), "wall_s": wall,
             "batched": {"batch": B, "value": batched_qps, "unit": "queries/s", "calls": nb},
@@ -345,6 +362,7 @@ def run_ours(args):
                     "steps": e2e_steps},
             "roofline": roof, "clocks": clk.summary(), "gpu_launches": agg["kernel_launches"],
             "phases_ms_per_query": {k: v / args.steps for k, v in phases.items()},
+            "randomized_probe": randomized,
             "serving": serving,
             "work": {"walks_per_query": agg["walks"] / args.steps, "tree_nodes_per_query": agg["tree_nodes"] / args.steps,
                      "vectors_per_query": agg["vectors"] / args.steps,

@@ -104,6 +104,10 @@ struct probesim_graph {
     uint64_t epoch = 0;
     Workspace ws0;
     size_t budget = 0;
+    // pull launch shape chosen by probesim_autotune (defaults until then)
+    int32_t tune_wide = 32;       // widest tile (16 or 32 columns)
+    int32_t tune_bps[33] = {0};   // blocks per SM per tile width (0 = default 8)
+    int32_t tuned = 0;
 };
 
 

@@ -115,6 +115,10 @@ void launch_trie_insert(const DeviceGraph &g, const QueryBatch &q, int32_t W, in
 void launch_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, int32_t *hcount, cudaStream_t s);
 void launch_sched_lists(TrieTable t, const int32_t *node_off, const int32_t *slot_off, const int32_t *dw, int32_t *ncur,
                         int32_t *node_list, int32_t *slot_entry, int32_t *nchild, int32_t *rho_slot, cudaStream_t s);
+void launch_sched_export(TrieTable t, int32_t *out, int32_t *count, cudaStream_t s);
+void launch_node_lists(TrieTable t, const int32_t *node_off, int32_t *ncur, int32_t *node_list, cudaStream_t s);
+void launch_set_slots(TrieTable t, const int32_t *pairs, int32_t count, cudaStream_t s);
+void launch_zero_listed(int32_t n, float *D, int32_t pitch, const int32_t *cols, int32_t count, cudaStream_t s);
 void launch_scan_exclusive(const int32_t *in, int32_t *out, int32_t count, cudaStream_t s);  // out has count+1
 void launch_sched_children(TrieTable t, const int32_t *slot_entry, int32_t S_total, const int32_t *slot_off,
                            const int32_t *child_off, int32_t *ccur, int32_t *child_list, cudaStream_t s);
@@ -124,11 +128,14 @@ void launch_dbuild(int32_t n, const float *MDp, int32_t pp, float *D, int32_t pd
 void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, int32_t pd, int32_t dw,
                           cudaStream_t s);
 void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, int32_t pitch,
-                    int32_t dw, cudaStream_t s);
+                    int32_t h0, cudaStream_t s);
+void launch_accumulate(int32_t n, float *B, int32_t pitch, const int32_t *gdst, const int32_t *goff, const int32_t *srcs,
+                       int32_t ngroups, cudaStream_t s);
 void launch_zero_cols(int32_t n, float *MD, int32_t pitch, int32_t c0, int32_t width, cudaStream_t s);
 void launch_zero_split_rows(const DeviceGraph &g, float *MD, int32_t pitch, int32_t width, cudaStream_t s);
-void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, float *MD, int32_t pitch, int32_t tile,
-                 cudaStream_t s);
+// pull MD[v][c] = w[v] * sum_{x in I(v)} D[x][c] for the columns c < width (a multiple of tile)
+void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, float *MD, int32_t pitch, int32_t width,
+                 int32_t tile, int32_t blocks_per_sm, cudaStream_t s);
 void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, const float *inv_nr,
                   const float *MD, int32_t pc, cudaStream_t s);
 void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,
@@ -203,8 +210,8 @@ void launch_i64_copy(const long long *a, int64_t *b, int64_t count, cudaStream_t
 // sets the message probesim_last_error() returns on the calling thread
 void set_last_error(const char *msg);
 
-// pull tile width for a vector count
-int32_t pull_tile_for(int32_t S);
+// pull tile width for a vector count (wide = the widest tile allowed, 16 or 32)
+int32_t pull_tile_for(int32_t S, int32_t wide = 32);
 inline int32_t round_up(int32_t x, int32_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace ps

@@ -123,6 +123,24 @@ void launch_dbuild(int32_t n, const float *MDp, int32_t pp, float *D, int32_t pd
     k_dbuild<<<blocks, 256, 0, s>>>(n, MDp, pp, D, pd, S, child_off, child_list);
 }
 
+// zero the listed columns of every row: one warp per row
+__global__ void __launch_bounds__(256) k_zero_listed(int32_t n, float *D, int32_t pitch, const int32_t *__restrict__ cols,
+                                                     int32_t count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        float *row = D + v * pitch;
+        for (int32_t c = lane; c < count; c += 32) row[__ldg(cols + c)] = 0.f;
+    }
+}
+
+void launch_zero_listed(int32_t n, float *D, int32_t pitch, const int32_t *cols, int32_t count, cudaStream_t s) {
+    if (count <= 0) return;
+    const int blocks = grid_for((int64_t)n * 32, 256, 8);
+    k_zero_listed<<<blocks, 256, 0, s>>>(n, D, pitch, cols, count);
+}
+
 // zero columns [c0, c0 + width) of every row: one warp per row
 __global__ void __launch_bounds__(256) k_zero_cols(int32_t n, float *MD, int32_t pitch, int32_t c0, int32_t width) {
     const int lane = threadIdx.x & 31;
@@ -166,13 +184,14 @@ void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float 
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_push_h2(const int64_t *__restrict__ out_off, const int32_t *__restrict__ out_col,
                                                  const float *__restrict__ w, const int32_t *__restrict__ nodes,
-                                                 int32_t cnt, TrieTable t, float *MD, int32_t pitch, int32_t dw) {
+                                                 int32_t cnt, TrieTable t, float *MD, int32_t pitch, int32_t h0) {
     const int lane = threadIdx.x & 31;
     const int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= cnt) return;
     const int32_t e = nodes[i];
-    const int32_t sl = t.slot[t.parent[t.parent[e]]];
-    if (sl < dw) return;
+    const int32_t p = t.parent[t.parent[e]];  // the height-2 node
+    const int32_t sl = t.slot[p];
+    if (sl < h0) return;
     const int32_t a = t.node[e];
     const float g = t.gamma[e];
     const int64_t beg = out_off[a], end = out_off[a + 1];
@@ -183,10 +202,55 @@ __global__ void __launch_bounds__(256) k_push_h2(const int64_t *__restrict__ out
 }
 
 void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, int32_t pitch,
-                    int32_t dw, cudaStream_t s) {
+                    int32_t h0, cudaStream_t s) {
     if (cnt <= 0) return;
     const int64_t threads = (int64_t)cnt * 32;
-    k_push_h2<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(g.out_off, g.out_col, g.w, nodes, cnt, t, MD, pitch, dw);
+    k_push_h2<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(g.out_off, g.out_col, g.w, nodes, cnt, t, MD, pitch, h0);
+}
+
+// ------------------------------------------------------------------------------------------------
+// accumulate: D of the dense nodes of a depth, in place in the previous level's MD buffer.  A dense node's
+// column already holds its heir's MD (the heir inherits the column); each group g adds (or, for a node
+// without heir, sets) the sum of its other children's columns: B[v][dst_g] (+)= sum of B[v][src], src in
+// srcs[off_g .. off_g+1).  One warp per row: every group's sum is formed before any column is written, so a
+// column that is both a source and a later destination is read first.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_accumulate(int32_t n, float *B, int32_t pitch, const int32_t *__restrict__ gdst,
+                                                    const int32_t *__restrict__ goff, const int32_t *__restrict__ srcs,
+                                                    int32_t ngroups) {
+    extern __shared__ float acc_sm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *mine = acc_sm + (size_t)wib * ngroups;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        float *row = B + v * pitch;
+        for (int32_t gi = lane; gi < ngroups; gi += 32) {
+            float sum = 0.f;
+            const int32_t e = __ldg(goff + gi + 1);
+            for (int32_t k = __ldg(goff + gi); k < e; ++k) sum += row[__ldg(srcs + k)];
+            mine[gi] = sum;
+        }
+        __syncwarp();
+        for (int32_t gi = lane; gi < ngroups; gi += 32) {
+            const int32_t d = __ldg(gdst + gi);
+            const int32_t c = d & 0x3fffffff;
+            row[c] = (d & (1 << 30)) ? mine[gi] : row[c] + mine[gi];  // bit 30: set (no heir)
+        }
+        __syncwarp();
+    }
+}
+
+void launch_accumulate(int32_t n, float *B, int32_t pitch, const int32_t *gdst, const int32_t *goff, const int32_t *srcs,
+                       int32_t ngroups, cudaStream_t s) {
+    if (ngroups <= 0) return;
+    int warps = 8;
+    while (warps > 1 && (size_t)warps * ngroups * 4 > 96 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * ngroups * 4;
+    cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const int threads = warps * 32;
+    const int blocks = grid_for((int64_t)n * 32, threads, 2048 / threads);
+    k_accumulate<<<blocks, threads, smem, s>>>(n, B, pitch, gdst, goff, srcs, ngroups);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -297,21 +361,21 @@ __global__ void __launch_bounds__(256) k_pull(const int32_t *__restrict__ piece_
     }
 }
 
-int32_t pull_tile_for(int32_t S) {
+int32_t pull_tile_for(int32_t S, int32_t wide) {
     if (S <= 1) return 1;
     if (S <= 2) return 2;
     if (S <= 4) return 4;
     if (S <= 8) return 8;
-    if (S <= 16) return 16;
+    if (S <= 16 || wide <= 16) return 16;
     return 32;
 }
 
-void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, float *MD, int32_t pitch, int32_t tile,
-                 cudaStream_t s) {
-    const int32_t ntiles = dpitch / tile;
+void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, float *MD, int32_t pitch, int32_t width,
+                 int32_t tile, int32_t blocks_per_sm, cudaStream_t s) {
+    const int32_t ntiles = width / tile;
     const int L = tile >= 4 ? tile / 4 : 1;
     const int64_t threads_needed = g.n_pieces * L;
-    const int blocks = grid_for(threads_needed, 256, 8);
+    const int blocks = grid_for(threads_needed, 256, blocks_per_sm > 0 ? blocks_per_sm : 8);
     dim3 grid(blocks, ntiles);
     switch (tile) {
         case 1: k_pull<1><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;

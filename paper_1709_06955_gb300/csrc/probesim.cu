@@ -9,6 +9,7 @@
 #include <shared_mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "engine.cuh"
@@ -408,7 +409,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     int64_t maxpitch = 1, maxdw = 1;
     for (int32_t d = 0; d < D1; ++d) {
         node_off[d + 1] = node_off[d] + ncount[d];
-        tile[d] = pull_tile_for(std::max(1, scount[d]));
+        tile[d] = pull_tile_for(std::max(1, scount[d]), g->tune_wide);
         dw[d] = scount[d] > 0 ? round_up(scount[d], tile[d]) : 0;
         cols[d] = dw[d] + hcount[d];
         pitch[d] = cols[d] > 0 ? round_up(cols[d], std::min(4, tile[d])) : 0;  // rows aligned for the pull's vectors
@@ -419,65 +420,185 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     const int32_t total_nodes = node_off[D1], S_total = slot_off[D1];
     ws->stats.tree_nodes += total_nodes;
     for (int32_t d = 0; d < D1; ++d) ws->stats.vectors += scount[d] + hcount[d];
-    const size_t level_bytes = (2 * (size_t)maxpitch + (size_t)maxdw) * (size_t)n * sizeof(float);
-    if (level_bytes > g->budget) {
+    PS_CUDA(ws->offs.ensure(sizeof(int32_t) * (D1 + 1)));
+    int32_t *d_node_off = ws->offs.as<int32_t>();
+    int32_t *h_offs = h_cnt + 3 * D1;
+    std::memcpy(h_offs, node_off.data(), sizeof(int32_t) * (D1 + 1));
+    PS_CUDA(cudaMemcpyAsync(d_node_off, h_offs, sizeof(int32_t) * (D1 + 1), cudaMemcpyHostToDevice, st));
+    PS_CUDA(ws->node_list.ensure(sizeof(int32_t) * std::max(1, total_nodes)));
+    ph.begin(1);
+    launch_node_lists(t, d_node_off, d_ncur, ws->node_list.as<int32_t>(), st);
+    // columns.  Every dense node's "heir" (its dense child with the deepest chain below it) takes over its
+    // column one depth down, so along a chain of heirs the MD column of the child already is the D column of
+    // the parent and nothing is copied.  Push columns (height 2) sit in a block after the dense columns.
+    int32_t ncol_nodes = 0;
+    for (int32_t d = 0; d < D1; ++d) ncol_nodes += scount[d] + hcount[d];
+    PS_CUDA(ws->slot_entry.ensure(sizeof(int32_t) * (5 * (size_t)std::max(1, ncol_nodes) + 1)));
+    int32_t *d_exp = ws->slot_entry.as<int32_t>(), *d_expn = d_exp + 5 * (size_t)std::max(1, ncol_nodes);
+    PS_CUDA(cudaMemsetAsync(d_expn, 0, sizeof(int32_t), st));
+    launch_sched_export(t, d_exp, d_expn, st);
+    ph.end();
+    launches += 2;
+    PS_CUDA(ws->pin_q.ensure(sizeof(int32_t) * (5 * (size_t)std::max(1, ncol_nodes) + 64)));
+    int32_t *h_exp = ws->pin_q.as<int32_t>();
+    PS_CUDA(cudaMemcpyAsync(h_exp, d_exp, sizeof(int32_t) * 5 * (size_t)ncol_nodes, cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    // export rows: 0 entry, 1 depth, 2 parent entry, 3 dense, 4 query
+    std::unordered_map<int32_t, int32_t> row_of;
+    row_of.reserve(2 * (size_t)ncol_nodes + 1);
+    std::vector<std::vector<int32_t>> dense_at(D1), push_at(D1);
+    for (int32_t i = 0; i < ncol_nodes; ++i) {
+        row_of[h_exp[5 * i]] = i;
+        (h_exp[5 * i + 3] ? dense_at : push_at)[h_exp[5 * i + 1]].push_back(i);
+    }
+    // heights are not exported; the heir is the dense child with the deepest dense descendant chain, found
+    // bottom-up, ties to the smaller entry
+    std::vector<int32_t> chain(ncol_nodes, 0), heir(ncol_nodes, -1), col(ncol_nodes, -1);
+    for (int32_t d = Dmax; d >= 1; --d)
+        for (int32_t i : dense_at[d]) {
+            const auto it = row_of.find(h_exp[5 * i + 2]);
+            if (it == row_of.end()) continue;
+            const int32_t pr = it->second;
+            const int32_t h = heir[pr];
+            if (h < 0 || chain[i] > chain[h] || (chain[i] == chain[h] && h_exp[5 * i] < h_exp[5 * h])) heir[pr] = i;
+            chain[pr] = std::max(chain[pr], chain[i] + 1);
+        }
+    // a chain is a maximal path of heirs; all its nodes share one column.  Chains are coloured deepest bottom
+    // first, each taking the smallest column whose chains all start below its bottom (every chain coloured
+    // before it ends at least as deep, so that is exactly "free over its depth range"); the columns in use at
+    // a depth then stay close to the number of dense nodes there.
+    std::vector<char> is_heir(ncol_nodes, 0);
+    for (int32_t i = 0; i < ncol_nodes; ++i)
+        if (heir[i] >= 0) is_heir[heir[i]] = 1;
+    struct Chain {
+        int32_t head, top, bottom;
+    };
+    std::vector<Chain> chains;
+    for (int32_t d = 0; d <= Dmax; ++d)
+        for (int32_t i : dense_at[d]) {
+            if (is_heir[i]) continue;
+            int32_t x = i, bot = d;
+            while (heir[x] >= 0) x = heir[x], ++bot;
+            chains.push_back({i, d, bot});
+        }
+    std::sort(chains.begin(), chains.end(), [&](const Chain &x, const Chain &y) {
+        if (x.bottom != y.bottom) return x.bottom > y.bottom;
+        if (x.top != y.top) return x.top < y.top;
+        return h_exp[5 * x.head] < h_exp[5 * y.head];
+    });
+    std::vector<int32_t> top_min;  // per column: the smallest top depth of the chains holding it
+    for (const Chain &ch : chains) {
+        int32_t c = 0;
+        while (c < (int32_t)top_min.size() && top_min[c] <= ch.bottom) ++c;
+        if (c == (int32_t)top_min.size()) top_min.push_back(ch.top);
+        top_min[c] = std::min(top_min[c], ch.top);
+        for (int32_t x = ch.head; x >= 0; x = heir[x]) col[x] = c;
+    }
+    std::vector<int32_t> width(D1, 0), rho(B, -1);
+    int32_t maxw = 0, maxh = 0;
+    for (int32_t d = 0; d <= Dmax; ++d) {
+        int32_t w = 0;
+        for (int32_t i : dense_at[d]) w = std::max(w, col[i] + 1);
+        width[d] = w;
+        maxw = std::max(maxw, w);
+        maxh = std::max(maxh, (int32_t)push_at[d].size());
+        if (d == 0)
+            for (int32_t i : dense_at[0]) rho[h_exp[5 * i + 4]] = col[i];
+    }
+    for (int32_t d = 0; d <= Dmax; ++d) {  // pull tile and the width it covers
+        tile[d] = pull_tile_for(std::max(1, width[d]), g->tune_wide);
+        dw[d] = width[d] > 0 ? round_up(width[d], tile[d]) : 0;
+    }
+    // MD of depth d is read in place as D of depth d-1, so its rows must hold the columns of both depths:
+    // pitch(d) = max(dw[d-1], dw[d]) dense columns, then the push block of depth d at h0[d]
+    std::vector<int32_t> h0v(D1, 0), rpv(D1, 0);
+    int64_t maxrp = 4;
+    for (int32_t d = 0; d <= Dmax; ++d) {
+        const int32_t dense_w = std::max(dw[d], d >= 1 ? dw[d - 1] : 0);
+        h0v[d] = round_up(std::max(dense_w, 1), 4);
+        rpv[d] = round_up(h0v[d] + (int32_t)push_at[d].size(), 4);
+        maxrp = std::max<int64_t>(maxrp, rpv[d]);
+    }
+    for (int32_t d = 0; d <= Dmax; ++d) {
+        std::vector<int32_t> &pa = push_at[d];
+        std::sort(pa.begin(), pa.end(), [&](int32_t x, int32_t y) { return h_exp[5 * x] < h_exp[5 * y]; });
+        for (size_t r = 0; r < pa.size(); ++r) col[pa[r]] = h0v[d] + (int32_t)r;
+    }
+    const size_t level_bytes2 = 2 * (size_t)maxrp * (size_t)n * sizeof(float);
+    if (level_bytes2 > g->budget) {
         *too_big = B > 1;
         return fail(PROBESIM_E_NOMEM, "score vectors of one query exceed the workspace budget");
     }
-    PS_CUDA(ws->offs.ensure(sizeof(int32_t) * 3 * (D1 + 1)));
-    int32_t *d_node_off = ws->offs.as<int32_t>(), *d_slot_off = d_node_off + D1 + 1, *d_dw = d_slot_off + D1 + 1;
-    int32_t *h_offs = h_cnt + 3 * D1;
-    std::memcpy(h_offs, node_off.data(), sizeof(int32_t) * (D1 + 1));
-    std::memcpy(h_offs + D1 + 1, slot_off.data(), sizeof(int32_t) * (D1 + 1));
-    std::memcpy(h_offs + 2 * (D1 + 1), dw.data(), sizeof(int32_t) * D1);
-    PS_CUDA(cudaMemcpyAsync(d_node_off, h_offs, sizeof(int32_t) * 3 * (D1 + 1), cudaMemcpyHostToDevice, st));
-    PS_CUDA(ws->node_list.ensure(sizeof(int32_t) * std::max(1, total_nodes)));
-    PS_CUDA(ws->slot_entry.ensure(sizeof(int32_t) * std::max(1, S_total)));
-    PS_CUDA(ws->nchild.ensure(sizeof(int32_t) * std::max(1, S_total)));
-    PS_CUDA(ws->child_off.ensure(sizeof(int32_t) * (S_total + 1)));
-    PS_CUDA(ws->child_list.ensure(sizeof(int32_t) * std::max(1, S_total)));
-    PS_CUDA(ws->ccur.ensure(sizeof(int32_t) * std::max(1, S_total)));
-    PS_CUDA(ws->rho_slot.ensure(sizeof(int32_t) * B));
-    ph.begin(1);
-    PS_CUDA(cudaMemsetAsync(ws->slot_entry.p, 0xFF, sizeof(int32_t) * std::max(1, S_total), st));
-    PS_CUDA(cudaMemsetAsync(ws->nchild.p, 0, sizeof(int32_t) * std::max(1, S_total), st));
-    PS_CUDA(cudaMemsetAsync(ws->ccur.p, 0, sizeof(int32_t) * std::max(1, S_total), st));
-    PS_CUDA(cudaMemsetAsync(ws->rho_slot.p, 0xFF, sizeof(int32_t) * B, st));
-    launch_sched_lists(t, d_node_off, d_slot_off, d_dw, d_ncur, ws->node_list.as<int32_t>(), ws->slot_entry.as<int32_t>(),
-                       ws->nchild.as<int32_t>(), ws->rho_slot.as<int32_t>(), st);
-    launch_scan_exclusive(ws->nchild.as<int32_t>(), ws->child_off.as<int32_t>(), S_total, st);
-    launch_sched_children(t, ws->slot_entry.as<int32_t>(), S_total, d_slot_off, ws->child_off.as<int32_t>(),
-                          ws->ccur.as<int32_t>(), ws->child_list.as<int32_t>(), st);
-    ph.end();
-    launches += 3;
-    // 4. level loop, deepest depth first.  MD buffers are [n][pitch]; D is [n][dw] (dense columns only).
-    PS_CUDA(ws->md_a.ensure((size_t)n * (size_t)maxpitch * sizeof(float)));
-    PS_CUDA(ws->md_b.ensure((size_t)n * (size_t)maxpitch * sizeof(float)));
-    PS_CUDA(ws->dmat.ensure((size_t)n * (size_t)maxdw * sizeof(float)));
-    float *prev = ws->md_a.as<float>(), *cur = ws->md_b.as<float>(), *Dm = ws->dmat.as<float>();
+    // accumulate groups per depth d (dense parents at d): dst = parent column (| set flag when it has no heir),
+    // srcs = columns (at d+1) of its children other than the heir
+    std::vector<std::vector<int32_t>> kids(ncol_nodes);
+    for (int32_t i = 0; i < ncol_nodes; ++i) {
+        const auto it = row_of.find(h_exp[5 * i + 2]);
+        if (it != row_of.end() && heir[it->second] != i) kids[it->second].push_back(col[i]);
+    }
+    std::vector<int32_t> pairs, gdst, goff, srcs, goff_at(D1 + 1, 0), gcount(D1, 0);
+    pairs.reserve(2 * (size_t)ncol_nodes);
+    for (int32_t i = 0; i < ncol_nodes; ++i) {
+        pairs.push_back(h_exp[5 * i]);
+        pairs.push_back(col[i]);
+    }
+    for (int32_t d = 0; d < D1; ++d) {
+        goff_at[d] = (int32_t)gdst.size();
+        if (d <= Dmax)
+            for (int32_t i : dense_at[d]) {
+                if (kids[i].empty() && heir[i] >= 0) continue;  // its column already is its heir's MD
+                gdst.push_back(col[i] | (heir[i] < 0 ? (1 << 30) : 0));
+                goff.push_back((int32_t)srcs.size());
+                srcs.insert(srcs.end(), kids[i].begin(), kids[i].end());
+            }
+        gcount[d] = (int32_t)gdst.size() - goff_at[d];
+    }
+    goff_at[D1] = (int32_t)gdst.size();
+    goff.push_back((int32_t)srcs.size());
+    // upload: slot pairs, group destinations, group offsets (global into srcs), sources, super-root columns
+    const size_t sched_ints = pairs.size() + gdst.size() + goff.size() + srcs.size() + B;
+    PS_CUDA(ws->child_list.ensure(sizeof(int32_t) * std::max<size_t>(1, sched_ints)));
+    PS_CUDA(ws->pin_q.ensure(sizeof(int32_t) * std::max<size_t>(1, sched_ints)));
+    int32_t *h_sched = ws->pin_q.as<int32_t>();
+    size_t o = 0;
+    auto put = [&](const std::vector<int32_t> &v) {
+        const size_t at = o;
+        if (!v.empty()) std::memcpy(h_sched + o, v.data(), sizeof(int32_t) * v.size());
+        o += v.size();
+        return at;
+    };
+    const size_t o_pairs = put(pairs), o_gdst = put(gdst), o_goff = put(goff), o_srcs = put(srcs), o_rho = put(rho);
+    int32_t *d_sched = ws->child_list.as<int32_t>();
+    PS_CUDA(cudaMemcpyAsync(d_sched, h_sched, sizeof(int32_t) * o, cudaMemcpyHostToDevice, st));
+    launch_set_slots(t, d_sched + o_pairs, (int32_t)(pairs.size() / 2), st);
+    ++launches;
+    const int32_t *d_rho = d_sched + o_rho;
+    // 4. level loop, deepest depth first.  Two MD buffers [n][P]: A receives this depth's MD; B holds the depth
+    // below, which becomes this depth's D in place (accumulate + gamma scatter) before the pull reads it.
+    PS_CUDA(ws->md_a.ensure((size_t)n * (size_t)maxrp * sizeof(float)));
+    PS_CUDA(ws->md_b.ensure((size_t)n * (size_t)maxrp * sizeof(float)));
+    float *A = ws->md_a.as<float>(), *Bm = ws->md_b.as<float>();
     const int32_t *node_list = ws->node_list.as<int32_t>();
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks;
     for (int32_t d = Dmax; d >= 0; --d) {
-        const int32_t S = scount[d], H = hcount[d], pd = pitch[d], wd = dw[d];
+        const int32_t S = scount[d], H = hcount[d], wd = dw[d];
+        const int32_t rp = rpv[d], rb = d + 1 <= Dmax ? rpv[d + 1] : 4, h0 = h0v[d], hb = d + 1 <= Dmax ? h0v[d + 1] : 0;
         if (S > 0) {
-            ph.begin(2);
-            if (d + 1 <= Dmax && cols[d + 1] > 0) {
-                launch_dbuild(n, prev, pitch[d + 1], Dm, wd, S, ws->child_off.as<int32_t>() + slot_off[d],
-                              ws->child_list.as<int32_t>(), st);
-                ++launches;
-            } else {
-                PS_CUDA(cudaMemsetAsync(Dm, 0, (size_t)n * wd * sizeof(float), st));
-            }
+            ph.begin(2);  // D of this depth's dense nodes, in place in B (the MD of depth d+1)
+            if (gcount[d] > 0)
+                launch_accumulate(n, Bm, rb, d_sched + o_gdst + goff_at[d], d_sched + o_goff + goff_at[d],
+                                  d_sched + o_srcs, gcount[d], st);
             ph.end();
+            ++launches;
             if (d + 2 <= Dmax) {
                 ph.begin(3);
-                launch_scatter_gamma(node_list + node_off[d + 2], ncount[d + 2], t, Dm, wd, wd, st);
+                launch_scatter_gamma(node_list + node_off[d + 2], ncount[d + 2], t, Bm, rb, hb > 0 ? hb : rb, st);
                 ph.end();
                 ++launches;
             }
             if (dg.n_split > 0) {
                 ph.begin(4);
-                launch_zero_split_rows(dg, cur, pd, wd, st);
+                launch_zero_split_rows(dg, A, rp, wd, st);
                 ph.end();
                 ++launches;
             }
@@ -487,7 +608,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
                 e1 = tm.get();
                 PS_CUDA(cudaEventRecord(e0, st));
             }
-            launch_pull(dg, Dm, wd, cur, pd, tile[d], st);
+            launch_pull(dg, Bm, rb, A, rp, wd, tile[d], g->tune_bps[tile[d]], st);
             ++launches;
             if (ws->profiling) {
                 PS_CUDA(cudaEventRecord(e1, st));
@@ -499,24 +620,25 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         }
         if (H > 0) {  // height-2 columns: zero, then push from the grandchildren's gamma
             ph.begin(6);
-            launch_zero_cols(n, cur, pd, wd, H, st);
-            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, cur, pd, wd, st);
+            launch_zero_cols(n, A, rp, h0, H, st);
+            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, A, rp, h0, st);
             ph.end();
-            ++launches;
+            launches += 2;
         }
         if (d >= 1) {
             ph.begin(7);
-            launch_gamma(dg, node_list + node_off[d], ncount[d], t, qb.inv_nr, cols[d] > 0 ? cur : nullptr, pd, st);
+            launch_gamma(dg, node_list + node_off[d], ncount[d], t, qb.inv_nr, (S + H) > 0 ? A : nullptr, rp, st);
             ph.end();
             ++launches;
         }
-        std::swap(prev, cur);
+        std::swap(A, Bm);
         ws->stats.levels += 1;
     }
+    float *MD0 = Bm;  // after the last swap, the super-roots' MD
+    (void)maxw;
     // 5. estimates: s(u, v) = MD(super-root)[v], s(u, u) = 1
     ph.begin(8);
-    launch_finalize(n, B, qb.node, ws->rho_slot.as<int32_t>(), cols[0] > 0 ? prev : nullptr, std::max(1, pitch[0]),
-                    dg.ext2int, d_out, st);
+    launch_finalize(n, B, qb.node, d_rho, scount[0] > 0 ? MD0 : nullptr, rpv[0], dg.ext2int, d_out, st);
     ph.end();
     ++launches;
     PS_CUDA(cudaGetLastError());
@@ -1056,6 +1178,61 @@ probesim_status probesim_topk(probesim_graph *g, const probesim_query *q, int32_
     std::shared_lock<std::shared_mutex> sl(g->store_mu);
     g_last_error.clear();
     return topk_core(g, &g->ws0, q, nq, kmax, ids, vals, (cudaStream_t)stream);
+}
+
+// Times the pull on this graph's in-lists for every tile width in {1, 2, 4, 8, 16, 32} and blocks-per-SM in
+// {2, 4, 8, 16} over a random score matrix, keeps the fastest shape per width, and picks the widest tile (16
+// or 32) by time per column.  The choice is stored in the graph and used by every later query.
+probesim_status probesim_autotune(probesim_graph *g, void *stream) {
+    if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
+    std::lock_guard<std::mutex> lk(g->mu);
+    std::shared_lock<std::shared_mutex> sl(g->store_mu);
+    g_last_error.clear();
+    cudaStream_t st = (cudaStream_t)stream;
+    const DeviceGraph &dg = g->dg;
+    const int32_t n = dg.n, P = 64;
+    Workspace *ws = &g->ws0;
+    PS_CUDA(ws->md_a.ensure((size_t)n * P * sizeof(float)));
+    PS_CUDA(ws->md_b.ensure((size_t)n * P * sizeof(float)));
+    PS_CUDA(cudaMemsetAsync(ws->md_a.p, 0x3c, (size_t)n * P * sizeof(float), st));  // any finite values
+    const int32_t tiles[] = {1, 2, 4, 8, 16, 32}, bpss[] = {2, 4, 8, 16};
+    Timer tm{ws, st};
+    double per_col[33] = {0};
+    for (int32_t T : tiles) {
+        double best = 1e30;
+        int32_t best_bps = 8;
+        for (int32_t bps : bpss) {
+            float total = 0.f;
+            for (int rep = 0; rep < 4; ++rep) {
+                cudaEvent_t e0 = tm.get(), e1 = tm.get();
+                PS_CUDA(cudaEventRecord(e0, st));
+                launch_pull(dg, ws->md_a.as<float>(), T, ws->md_b.as<float>(), P, T, T, bps, st);
+                PS_CUDA(cudaEventRecord(e1, st));
+                PS_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) total += ms;  // the first run warms the caches
+            }
+            if (total < best) {
+                best = total;
+                best_bps = bps;
+            }
+        }
+        g->tune_bps[T] = best_bps;
+        per_col[T] = best / 3.0 / T;
+    }
+    g->tune_wide = per_col[16] < per_col[32] ? 16 : 32;
+    g->tuned = 1;
+    PS_CUDA(cudaGetLastError());
+    return PROBESIM_OK;
+}
+
+probesim_status probesim_get_tuning(const probesim_graph *g, int32_t *wide_tile, int32_t *blocks_per_sm) {
+    if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
+    if (wide_tile) *wide_tile = g->tune_wide;
+    if (blocks_per_sm)
+        for (int i = 0; i < 6; ++i) blocks_per_sm[i] = g->tune_bps[1 << i] ? g->tune_bps[1 << i] : 8;
+    return PROBESIM_OK;
 }
 
 probesim_status probesim_set_profiling(probesim_graph *g, int32_t on) {

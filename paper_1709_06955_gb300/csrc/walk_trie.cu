@@ -185,6 +185,48 @@ void launch_sched_lists(TrieTable t, const int32_t *node_off, const int32_t *slo
                                                                  nchild, rho_slot);
 }
 
+// Exports every node that owns a column (dense or push): entry, depth, parent entry, dense flag, query.
+__global__ void k_sched_export(TrieTable t, int32_t *out, int32_t *count) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= t.cap) return;
+    if (t.key[e] == kEmptyKey) return;
+    const int32_t sl = t.slot[e];
+    if (sl == -1) return;
+    const int32_t i = atomicAdd(count, 1);
+    out[5 * i + 0] = (int32_t)e;
+    out[5 * i + 1] = t.depth[e];
+    out[5 * i + 2] = t.parent[e];
+    out[5 * i + 3] = sl >= 0 ? 1 : 0;
+    out[5 * i + 4] = t.query[e];
+}
+
+void launch_sched_export(TrieTable t, int32_t *out, int32_t *count, cudaStream_t s) {
+    k_sched_export<<<(unsigned)((t.cap + 255) / 256), 256, 0, s>>>(t, out, count);
+}
+
+// Node lists per depth (every tree node).
+__global__ void k_node_lists(TrieTable t, const int32_t *__restrict__ node_off, int32_t *ncur, int32_t *node_list) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= t.cap) return;
+    if (t.key[e] == kEmptyKey) return;
+    const int32_t d = t.depth[e];
+    node_list[node_off[d] + atomicAdd(&ncur[d], 1)] = (int32_t)e;
+}
+
+void launch_node_lists(TrieTable t, const int32_t *node_off, int32_t *ncur, int32_t *node_list, cudaStream_t s) {
+    k_node_lists<<<(unsigned)((t.cap + 255) / 256), 256, 0, s>>>(t, node_off, ncur, node_list);
+}
+
+// slot[pairs[2i]] = pairs[2i+1]
+__global__ void k_set_slots(TrieTable t, const int32_t *__restrict__ pairs, int32_t count) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) t.slot[pairs[2 * i]] = pairs[2 * i + 1];
+}
+
+void launch_set_slots(TrieTable t, const int32_t *pairs, int32_t count, cudaStream_t s) {
+    if (count > 0) k_set_slots<<<(count + 255) / 256, 256, 0, s>>>(t, pairs, count);
+}
+
 // Single-block exclusive scan: out[0..count] with out[count] = total.
 __global__ void __launch_bounds__(1024) k_scan_exclusive(const int32_t *__restrict__ in, int32_t *__restrict__ out,
                                                          int32_t count) {

@@ -21,7 +21,7 @@ EXPORTS = [
     "probesim_single_source", "probesim_topk", "probesim_set_profiling", "probesim_get_stats",
     "probesim_last_error", "probesim_topk_select_noalloc", "probesim_server_config_default",
     "probesim_server_create", "probesim_server_submit", "probesim_server_update", "probesim_server_poll",
-    "probesim_server_get_stats", "probesim_server_destroy",
+    "probesim_server_get_stats", "probesim_server_destroy", "probesim_autotune", "probesim_get_tuning",
 ]
 
 
@@ -110,6 +110,8 @@ def load(path=None):
     L.probesim_server_poll.argtypes = [vp, C.c_int32, C.c_int32, P(Result), vp, vp, P(C.c_int32), C.c_int32]
     L.probesim_server_get_stats.argtypes = [vp, P(ServerStats)]
     L.probesim_server_destroy.argtypes = [vp]
+    L.probesim_autotune.argtypes = [vp, vp]
+    L.probesim_get_tuning.argtypes = [vp, P(C.c_int32), P(C.c_int32)]
     for name in EXPORTS:
         if name != "probesim_last_error":
             getattr(L, name).restype = C.c_int
@@ -274,6 +276,17 @@ class Graph:
             vals = np.zeros((nq, kmax), np.float32)
         _check(load().probesim_topk(self._h, queries, nq, kmax, _ptr(ids), _ptr(vals), _stream(stream)))
         return ids, vals
+
+    def autotune(self, stream=None):
+        """Times the pull launch shapes on this graph and keeps the fastest (probesim_autotune)."""
+        _check(load().probesim_autotune(self._h, _stream(stream)))
+        return self.tuning()
+
+    def tuning(self):
+        wide = C.c_int32()
+        bps = (C.c_int32 * 6)()
+        _check(load().probesim_get_tuning(self._h, C.byref(wide), bps))
+        return {"wide_tile": wide.value, "blocks_per_sm": {1 << i: bps[i] for i in range(6)}}
 
     def set_profiling(self, on=True):
         _check(load().probesim_set_profiling(self._h, 1 if on else 0))

@@ -252,3 +252,15 @@ def test_errors(cfg1):
     with pytest.raises(probesim.ProbeSimError) as e:
         probesim.Graph(10, np.array([0], np.int32), np.array([1], np.int32), l_max=0)
     assert e.value.status == probesim.E_INVALID
+
+
+def test_autotune_keeps_results(cfg1):
+    n, s, d, _, O = cfg1
+    G = gpu_graph(n, s, d)
+    tune = G.autotune()
+    assert tune["wide_tile"] in (16, 32) and all(b in (2, 4, 8, 16) for b in tune["blocks_per_sm"].values())
+    qs = synth.queries(n, d, 3, seed=41)
+    out = G.single_source(_q(qs, eps=0.1, query_ids=[1, 2, 3]))
+    for t, u in enumerate(qs):
+        ref, _ = O.single_source(int(u), eps=0.1, seed=3, qid=1 + t)
+        assert np.max(np.abs(out[t] - ref)) <= TOL
