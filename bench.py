@@ -298,18 +298,23 @@ def run_ours(args):
 
     # randomized PROBE (Alg. 3) on the same graph: a few queries one at a time
     GR = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_RANDOMIZED)
-    rq = 5
+    rq = 10
     GR.single_source(query(0), out=out, stream=sptr)
-    barrier()
-    r0 = time.perf_counter()
+    rsum = {"edge_gathers": 0, "levels": 0, "walk_nodes": 0}
+    rand_s = 0.0
     for i in range(rq):
+        barrier()
+        r0 = time.perf_counter()
         GR.single_source(query(args.warmup + i), out=out, stream=sptr)
-    barrier()
-    rand_s = time.perf_counter() - r0
-    rstats = GR.stats()
+        barrier()
+        rand_s += time.perf_counter() - r0
+        rst = GR.stats()  # describes the last call
+        for k in rsum:
+            rsum[k] += rst[k]
     GR.close()
     randomized = {"value": rq / rand_s, "unit": "queries/s", "queries": rq,
-                  "candidates_per_query": rstats["edge_gathers"], "levels_per_query": rstats["levels"]}
+                  "candidates_per_query": rsum["edge_gathers"] / rq, "levels_per_query": rsum["levels"] / rq,
+                  "walk_nodes_per_query": rsum["walk_nodes"] / rq}
 
     # serving leg: Poisson arrivals into the continuous-batching server (top-k, k in {10, 50, 100})
     serving = serving_leg(probesim, G, qs, args.serve_rate, args.serve_seconds, rank)

@@ -317,7 +317,7 @@ __device__ __forceinline__ void vstore(float *p, float2 v) { *reinterpret_cast<f
 __device__ __forceinline__ void vstore(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
 template <int T>
-__global__ void __launch_bounds__(256) k_pull(const int32_t *__restrict__ piece_v, const int64_t *__restrict__ piece_beg,
+__global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const int32_t *__restrict__ piece_v, const int64_t *__restrict__ piece_beg,
                                               const int32_t *__restrict__ piece_len, int64_t n_pieces,
                                               const int32_t *__restrict__ in_col, const float *__restrict__ w,
                                               const float *__restrict__ D, int32_t dpitch, float *__restrict__ MD,
@@ -333,31 +333,59 @@ __global__ void __launch_bounds__(256) k_pull(const int32_t *__restrict__ piece_
     const int32_t col0 = blockIdx.y * T + lig * VEC;
     const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L;
     const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / L;
-    for (int64_t p = gid; p < n_pieces; p += ngroups) {
-        const int32_t v = __ldg(piece_v + p);
-        const int64_t beg = __ldg(piece_beg + p);
-        const int32_t info = __ldg(piece_len + p);
+    // Software pipeline over this group's pieces p, p + ngroups, ...: the metadata of the piece after next and
+    // the column indices of the next chunk (or of the next piece's first chunk) are loaded while the current
+    // chunk's row gathers are in flight, so a short piece costs about one gather round trip.
+    auto load_meta = [&](int64_t q, int32_t &v, int64_t &beg, int32_t &info) {
+        if (q < n_pieces) {
+            v = __ldg(piece_v + q);
+            beg = __ldg(piece_beg + q);
+            info = __ldg(piece_len + q);
+        } else {
+            v = 0, beg = 0, info = 0;
+        }
+    };
+    auto load_idx = [&](int64_t beg, int32_t len, int32_t e0, int32_t(&mine)[PER]) {
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int32_t e = e0 + lig + L * r;
+            mine[r] = e < len ? __ldg(in_col + beg + e) : -1;
+        }
+    };
+    int64_t p = gid;
+    int32_t v, info, v1, info1;
+    int64_t beg, beg1;
+    load_meta(p, v, beg, info);
+    load_meta(p + ngroups, v1, beg1, info1);
+    int32_t mine[PER];
+    load_idx(beg, info & 0x7fffffff, 0, mine);
+    for (; p < n_pieces; p += ngroups) {
+        int32_t v2, info2;
+        int64_t beg2;
+        load_meta(p + 2 * ngroups, v2, beg2, info2);
+        const float wv = __ldg(w + v);
         const int32_t len = info & 0x7fffffff;
         V acc = vzero<V>();
-        for (int32_t e0 = 0; e0 < len; e0 += CH) {
-            int32_t mine[PER];
-#pragma unroll
-            for (int r = 0; r < PER; ++r) {
-                const int32_t e = e0 + lig + L * r;
-                mine[r] = e < len ? __ldg(in_col + beg + e) : -1;
-            }
+        for (int32_t e0 = 0;;) {
             V val[CH];
 #pragma unroll
             for (int j = 0; j < CH; ++j) {
                 const int32_t x = L == 1 ? mine[j] : __shfl_sync(gmask, mine[j / L], j % L, L);
                 val[j] = x >= 0 ? VecT<VEC>::load(D + (int64_t)x * dpitch + col0) : vzero<V>();
             }
+            e0 += CH;
+            const bool more = e0 < len;
+            if (more) load_idx(beg, len, e0, mine);
+            else load_idx(beg1, info1 & 0x7fffffff, 0, mine);
 #pragma unroll
             for (int j = 0; j < CH; ++j) vadd(acc, val[j]);
+            if (!more) break;
         }
-        const V res = vscale(acc, __ldg(w + v));
+        const V res = vscale(acc, wv);
         float *dst = MD + (int64_t)v * pitch + col0;
         if (info < 0) vatomic(dst, res); else vstore(dst, res);
+        v = v1, beg = beg1, info = info1;
+        v1 = v2, beg1 = beg2, info1 = info2;
     }
 }
 
