@@ -136,16 +136,17 @@ typedef struct {
                                score per vector-edge, 4 per written score, 12 per vertex per tile */
     int64_t kernel_launches;/* all kernels this library launched in the call */
     double phase_ms[12];    /* profiling on: CUDA-event time per phase of the deterministic path: 0 walks,
-                               1 walk tree and level schedule, 2 D build, 3 gamma scatter, 4 split-row zeroing,
-                               5 pull, 6 push columns, 7 gamma, 8 estimates; 9-11 unused */
+                               1 walk tree and level schedule, 2 D accumulate, 3 gamma scatter, 4 split-row
+                               zeroing, 5 pull, 6 push columns, 7 gamma, 8 estimates; 9-11 unused */
+    int64_t max_columns;    /* widest score matrix of the level loop, in columns (deterministic path) */
 } probesim_stats;
 
 probesim_status probesim_set_profiling(probesim_graph *g, int32_t on);
 
 /* Autotuner of the PROBE level kernel's launch shape on this graph.  It times the pull over the graph's own
- * in-lists for tile widths {1,2,4,8,16,32} columns and {2,4,8,16} blocks per SM (a random 64-column score
- * matrix, CUDA events, best of 3 after a warm-up), keeps the fastest shape per width and the widest tile
- * (16 or 32) with the lower time per column.  Later queries on the graph use the choice.  Takes about a
+ * in-lists for tile widths {1,2,4,8,16,32} columns and {2,4,8,16} blocks per SM (a constant-filled 64-column
+ * score matrix, CUDA events, three runs after a warm-up), keeps the fastest shape per width and, for the
+ * 32-column tiles of wide matrices, whichever of 32-column tiles and 16-column halves takes less time.  Later queries on the graph use the choice.  Takes about a
  * second; results do not depend on it (only summation order). */
 probesim_status probesim_autotune(probesim_graph *g, void *stream);
 /* The current choice: *wide_tile in {16, 32}; blocks_per_sm[6] for tile widths 1, 2, 4, 8, 16, 32. */

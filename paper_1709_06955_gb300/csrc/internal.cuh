@@ -105,6 +105,46 @@ struct LaunchCounters {
     int32_t overflow;  // hash table full
 };
 
+// Column layout of the score matrix of one depth ([n] rows x pitch columns, FP32).  Up to kGroup columns
+// it is plain node-major, [n][pitch].  Wider matrices are cut into groups of kGroup columns, each group one
+// [n][kGroup] block (1 KB rows), stored group after group with a stride of gs floats (n * kGroup plus a
+// few cache lines, so equal rows of different groups do not map to the same memory partition).  A pull
+// tile of 32 columns then gathers 128 B per row from inside one block of n KB whatever the total width,
+// while the kernels that touch many columns of one row (accumulate, gamma) still find them in one row.
+constexpr int32_t kGroup = 256;
+constexpr int64_t kGroupSkew = 5 * 32;  // floats: five 128-byte lines
+
+struct ColLayout {
+    int64_t n = 0;
+    int32_t K = 0;   // number of groups; 0 for a node-major matrix
+    int32_t R = 0;   // row pitch of a node-major matrix
+    int64_t gs = 0;  // group stride in floats
+    __host__ __device__ int64_t base(int32_t c) const {  // offset of (row 0, column c)
+        return K > 0 ? (int64_t)(c / kGroup) * gs + (c % kGroup) : (int64_t)c;
+    }
+    __host__ __device__ int32_t rpitch(int32_t) const { return K > 0 ? kGroup : R; }  // row pitch at column c
+    __host__ __device__ int64_t at(int64_t v, int32_t c) const {
+        return K > 0 ? (int64_t)(c / kGroup) * gs + v * kGroup + (c % kGroup) : v * R + c;
+    }
+    __host__ __device__ int64_t size() const { return K > 0 ? (int64_t)K * gs : (int64_t)R * n; }
+    // a pull over consecutive tiles of T columns starting at column 0: tile j starts (j / sub) * ts + (j % sub)
+    // * T floats after column 0
+    int64_t tile_stride() const { return K > 0 ? gs : 0; }
+    int32_t tile_sub(int32_t T) const { return K > 0 ? kGroup / T : (1 << 30); }
+};
+// the layout of a matrix with at least `cols` columns (cols a multiple of 4)
+inline ColLayout make_layout(int32_t n, int32_t cols) {
+    ColLayout L;
+    L.n = n;
+    if (cols <= kGroup) {
+        L.R = cols;
+    } else {
+        L.K = (cols + kGroup - 1) / kGroup;
+        L.gs = (int64_t)n * kGroup + kGroupSkew;
+    }
+    return L;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Launchers (each launches one kernel on `s`).
 // ---------------------------------------------------------------------------------------------
@@ -113,33 +153,28 @@ void launch_walks(const DeviceGraph &g, const QueryBatch &q, int32_t W, int32_t 
 void launch_trie_insert(const DeviceGraph &g, const QueryBatch &q, int32_t W, int32_t l_max, const int32_t *walks,
                         const int32_t *lens, TrieTable t, LaunchCounters *ctr, cudaStream_t s);
 void launch_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, int32_t *hcount, cudaStream_t s);
-void launch_sched_lists(TrieTable t, const int32_t *node_off, const int32_t *slot_off, const int32_t *dw, int32_t *ncur,
-                        int32_t *node_list, int32_t *slot_entry, int32_t *nchild, int32_t *rho_slot, cudaStream_t s);
 void launch_sched_export(TrieTable t, int32_t *out, int32_t *count, cudaStream_t s);
 void launch_node_lists(TrieTable t, const int32_t *node_off, int32_t *ncur, int32_t *node_list, cudaStream_t s);
 void launch_set_slots(TrieTable t, const int32_t *pairs, int32_t count, cudaStream_t s);
-void launch_zero_listed(int32_t n, float *D, int32_t pitch, const int32_t *cols, int32_t count, cudaStream_t s);
-void launch_scan_exclusive(const int32_t *in, int32_t *out, int32_t count, cudaStream_t s);  // out has count+1
-void launch_sched_children(TrieTable t, const int32_t *slot_entry, int32_t S_total, const int32_t *slot_off,
-                           const int32_t *child_off, int32_t *ccur, int32_t *child_list, cudaStream_t s);
-
-void launch_dbuild(int32_t n, const float *MDp, int32_t pp, float *D, int32_t pd, int32_t S, const int32_t *child_off,
-                   const int32_t *child_list, cudaStream_t s);
-void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, int32_t pd, int32_t dw,
+void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, ColLayout L, int32_t h0,
                           cudaStream_t s);
-void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, int32_t pitch,
+void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, ColLayout L,
                     int32_t h0, cudaStream_t s);
-void launch_accumulate(int32_t n, float *B, int32_t pitch, const int32_t *gdst, const int32_t *goff, const int32_t *srcs,
-                       int32_t ngroups, cudaStream_t s);
-void launch_zero_cols(int32_t n, float *MD, int32_t pitch, int32_t c0, int32_t width, cudaStream_t s);
-void launch_zero_split_rows(const DeviceGraph &g, float *MD, int32_t pitch, int32_t width, cudaStream_t s);
-// pull MD[v][c] = w[v] * sum_{x in I(v)} D[x][c] for the columns c < width (a multiple of tile)
-void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, float *MD, int32_t pitch, int32_t width,
-                 int32_t tile, int32_t blocks_per_sm, cudaStream_t s);
+// wdense: the destinations are columns < wdense
+void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *gdst, const int32_t *goff,
+                       const int32_t *srcs, int32_t ngroups, cudaStream_t s);
+void launch_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width, cudaStream_t s);
+void launch_zero_split_rows(const DeviceGraph &g, float *MD, ColLayout L, int32_t width, cudaStream_t s);
+// pull MD[v][c] = w[v] * sum_{x in I(v)} D[x][c] over ntiles tiles of `tile` columns.  D and MD point at the
+// first tile's column in row 0; their rows are dpitch / pitch floats apart; tile j of D starts (j / dsub) * dts +
+// (j % dsub) * tile floats after the first, and likewise for MD with mts / msub (ColLayout::tile_stride/sub).
+void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t dts, int32_t dsub, float *MD,
+                 int32_t pitch, int64_t mts, int32_t msub, int32_t ntiles, int32_t tile, int32_t blocks_per_sm,
+                 cudaStream_t s);
 void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, const float *inv_nr,
-                  const float *MD, int32_t pc, cudaStream_t s);
+                  const float *MD, ColLayout L, cudaStream_t s);
 void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,
-                     int32_t p0, const int32_t *ext2int, float *out, cudaStream_t s);
+                     ColLayout L, const int32_t *ext2int, float *out, cudaStream_t s);
 // ids[i] = map[ids[i]] for ids[i] >= 0
 void launch_map_ids(int32_t *ids, int64_t count, const int32_t *map, cudaStream_t s);
 

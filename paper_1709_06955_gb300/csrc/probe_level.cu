@@ -14,42 +14,19 @@
 // pull; for height 2, D(t) is just the gamma terms of t's grandchildren (all leaves), so the column is
 // "pushed": MD(t) = sum_g gamma_g * sum_{x in O(a_g)} sqrt(c)/|I(x)| e_x.  The level loop runs from the
 // deepest depth to the virtual super-root (depth 0, whose only child is the root u):
-//   dbuild   D(t)[x]  = sum of the children's MD columns                (segmented row sums, dense t)
+//   accumulate D(t)[x] = sum of the children's MD columns, in place      (dense t; an heir's column is reused)
 //   scatter  D(t)[a_g] += gamma_g for every grandchild g of t            (sparse terms, dense t)
 //   pull     MD(t)[v] = sqrt(c)/|I(v)| * sum_{x in I(v)} D(t)[x]         (the dominant kernel, dense t)
 //   push     MD(t)[x] += sqrt(c)/|I(x)| * gamma_g, x in O(a_g)           (height-2 t)
 //   gamma    gamma_t  = w_t/n_r - sqrt(c)/|I(a_t)| * (sum_{x in I(a_t)} MD(t)[x] + G_t),  G_parent += gamma_t
 // The result is exactly Alg. 4's (up to FP32 rounding); the work is one pull per slot instead of
-// q-1 pushes per tree node.  Score vectors of one depth are stored node-major, [n][pitch] FP32.
+// q-1 pushes per tree node.  The score vectors of one depth form an [n] x pitch FP32 matrix in the ColLayout
+// of internal.cuh: node-major up to 256 columns, else groups of 256 columns, each an [n][256] block.
 #include <algorithm>
 
 #include "internal.cuh"
 
 namespace ps {
-
-// ------------------------------------------------------------------------------------------------
-// dbuild: one warp per row x; D[x][p] = sum_{c in children(p)} MDp[x][c], zero for padding columns.
-// ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_dbuild(int32_t n, const float *__restrict__ MDp, int32_t pp,
-                                                float *__restrict__ D, int32_t pd, int32_t S,
-                                                const int32_t *__restrict__ child_off,
-                                                const int32_t *__restrict__ child_list) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t x = warp; x < n; x += nwarps) {
-        const float *src = MDp + x * pp;
-        float *dst = D + x * pd;
-        for (int32_t p = lane; p < pd; p += 32) {
-            float acc = 0.f;
-            if (p < S) {
-                const int32_t cb = __ldg(child_off + p), ce = __ldg(child_off + p + 1);
-                for (int32_t c = cb; c < ce; ++c) acc += __ldg(src + __ldg(child_list + c));
-            }
-            dst[p] = acc;
-        }
-    }
-}
 
 static int grid_for(int64_t work, int threads, int per_sm) {
     int dev = 0, sms = 152;
@@ -61,213 +38,239 @@ static int grid_for(int64_t work, int threads, int per_sm) {
     return (int)(blocks < 1 ? 1 : blocks);
 }
 
-// dbuild through shared memory: a block copies R consecutive rows of MDp (one contiguous range of about 32 KB,
-// whatever the width) into shared memory and forms the R output rows of D (one contiguous range) from it,
-// one output element per thread and step; the depth's child lists sit in shared memory.  Both global
-// transfers are fully coalesced.
-constexpr int kDbThreads = 256;
-
-__global__ void __launch_bounds__(kDbThreads) k_dbuild_smem(int32_t n, const float *__restrict__ MDp, int32_t pp,
-                                                            float *__restrict__ D, int32_t pd, int32_t S,
-                                                            const int32_t *__restrict__ child_off,
-                                                            const int32_t *__restrict__ child_list, int32_t R) {
-    extern __shared__ float sm[];
-    float *rows = sm;
-    int32_t *s_off = reinterpret_cast<int32_t *>(sm + (size_t)R * pp);
-    int32_t *s_list = s_off + (S + 1);
-    const int32_t base = child_off[0], nk = child_off[S] - base;
-    for (int32_t i = threadIdx.x; i <= S; i += blockDim.x) s_off[i] = child_off[i] - base;
-    for (int32_t i = threadIdx.x; i < nk; i += blockDim.x) s_list[i] = child_list[base + i];
-    __syncthreads();
-    for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < n; r0 += (int64_t)gridDim.x * R) {
-        const int32_t nr = (int32_t)min((int64_t)R, (int64_t)n - r0);
-        const int32_t cnt = nr * pp;
-        const float *src = MDp + r0 * pp;
-        if ((pp & 3) == 0) {
-            const float4 *s4 = reinterpret_cast<const float4 *>(src);
-            float4 *d4 = reinterpret_cast<float4 *>(rows);
-            for (int32_t i = threadIdx.x; i < cnt / 4; i += blockDim.x) d4[i] = __ldcs(s4 + i);
-        } else {
-            for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) rows[i] = __ldcs(src + i);
-        }
-        __syncthreads();
-        float *dst = D + r0 * pd;
-        const int32_t ocnt = nr * pd;
-        for (int32_t o = threadIdx.x; o < ocnt; o += blockDim.x) {
-            const int32_t r = o / pd, p = o - r * pd;
-            float acc = 0.f;
-            if (p < S) {
-                const float *row = rows + r * pp;
-                const int32_t ce = s_off[p + 1];
-                for (int32_t c = s_off[p]; c < ce; ++c) acc += row[s_list[c]];
-            }
-            __stcs(dst + o, acc);
-        }
-        __syncthreads();
+// zero columns [c0, c0 + width) of every row; consecutive threads take consecutive columns of a row
+__global__ void k_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width) {
+    const int64_t total = (int64_t)n * width;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = i / width;
+        const int32_t c = c0 + (int32_t)(i - v * width);
+        MD[L.at(v, c)] = 0.f;
     }
 }
 
-void launch_dbuild(int32_t n, const float *MDp, int32_t pp, float *D, int32_t pd, int32_t S, const int32_t *child_off,
-                   const int32_t *child_list, cudaStream_t s) {
-    // rows per block step: about 32 KB of MDp rows at any width; the child lists need (S + 1 + children) ints,
-    // children <= pp
-    const int32_t R = (int32_t)std::max<int64_t>(1, std::min<int64_t>(4096, 8192 / std::max(1, pp)));
-    const int64_t smem = 4 * (int64_t)R * pp + 4 * ((int64_t)S + 1 + pp);
-    if (smem <= 160 * 1024 && (int64_t)R * std::max(pp, pd) < ((int64_t)1 << 30)) {
-        cudaFuncSetAttribute(k_dbuild_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        const int blocks = grid_for((int64_t)(n + R - 1) / R * kDbThreads, kDbThreads, 4);
-        k_dbuild_smem<<<blocks, kDbThreads, (size_t)smem, s>>>(n, MDp, pp, D, pd, S, child_off, child_list, R);
-        return;
-    }
-    const int blocks = grid_for((int64_t)n * 32, 256, 8);
-    k_dbuild<<<blocks, 256, 0, s>>>(n, MDp, pp, D, pd, S, child_off, child_list);
-}
-
-// zero the listed columns of every row: one warp per row
-__global__ void __launch_bounds__(256) k_zero_listed(int32_t n, float *D, int32_t pitch, const int32_t *__restrict__ cols,
-                                                     int32_t count) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp; v < n; v += nwarps) {
-        float *row = D + v * pitch;
-        for (int32_t c = lane; c < count; c += 32) row[__ldg(cols + c)] = 0.f;
-    }
-}
-
-void launch_zero_listed(int32_t n, float *D, int32_t pitch, const int32_t *cols, int32_t count, cudaStream_t s) {
-    if (count <= 0) return;
-    const int blocks = grid_for((int64_t)n * 32, 256, 8);
-    k_zero_listed<<<blocks, 256, 0, s>>>(n, D, pitch, cols, count);
-}
-
-// zero columns [c0, c0 + width) of every row: one warp per row
-__global__ void __launch_bounds__(256) k_zero_cols(int32_t n, float *MD, int32_t pitch, int32_t c0, int32_t width) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp; v < n; v += nwarps) {
-        float *row = MD + v * pitch + c0;
-        for (int32_t c = lane; c < width; c += 32) row[c] = 0.f;
-    }
-}
-
-void launch_zero_cols(int32_t n, float *MD, int32_t pitch, int32_t c0, int32_t width, cudaStream_t s) {
+void launch_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width, cudaStream_t s) {
     if (width <= 0) return;
-    const int blocks = grid_for((int64_t)n * 32, 256, 8);
-    k_zero_cols<<<blocks, 256, 0, s>>>(n, MD, pitch, c0, width);
+    const int blocks = grid_for((int64_t)n * width, 256, 8);
+    k_zero_cols<<<blocks, 256, 0, s>>>(n, MD, L, c0, width);
 }
 
 // ------------------------------------------------------------------------------------------------
-// scatter: for every tree node g at depth t+2 whose grandparent has a dense column (< dw),
-// D[a_g][slot(grandparent(g))] += gamma_g.
+// scatter: for every tree node g at depth t+2 whose grandparent has a dense column (< h0, the first push
+// column of the grandparent's depth), D[a_g][slot(grandparent(g))] += gamma_g.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_scatter_gamma(const int32_t *__restrict__ nodes, int32_t cnt, TrieTable t, float *D, int32_t pd,
-                                int32_t dw) {
+__global__ void k_scatter_gamma(const int32_t *__restrict__ nodes, int32_t cnt, TrieTable t, float *D, ColLayout L,
+                                int32_t h0) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cnt) return;
     const int32_t e = nodes[i];
     const int32_t sl = t.slot[t.parent[t.parent[e]]];
-    if (sl < 0 || sl >= dw) return;
-    atomicAdd(D + (int64_t)t.node[e] * pd + sl, t.gamma[e]);
+    if (sl < 0 || sl >= h0) return;
+    atomicAdd(D + L.at(t.node[e], sl), t.gamma[e]);
 }
 
-void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, int32_t pd, int32_t dw,
+void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, ColLayout L, int32_t h0,
                           cudaStream_t s) {
     if (cnt <= 0) return;
-    k_scatter_gamma<<<(cnt + 255) / 256, 256, 0, s>>>(nodes, cnt, t, D, pd, dw);
+    k_scatter_gamma<<<(cnt + 255) / 256, 256, 0, s>>>(nodes, cnt, t, D, L, h0);
 }
 
 // ------------------------------------------------------------------------------------------------
-// push: one warp per tree node g at depth t+2 whose grandparent p has a push column (>= dw):
-// MD[x][slot(p)] += sqrt(c)/|I(x)| * gamma_g for every x in O(a_g).
+// push: for every tree node g at depth t+2 whose grandparent p has a push column (>= h0):
+// MD[x][slot(p)] += sqrt(c)/|I(x)| * gamma_g for every x in O(a_g).  One block per node g: an out-list can
+// hold tens of thousands of edges (hubs), so the block's threads split it and a hub does not hold up the
+// launch.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_push_h2(const int64_t *__restrict__ out_off, const int32_t *__restrict__ out_col,
-                                                 const float *__restrict__ w, const int32_t *__restrict__ nodes,
-                                                 int32_t cnt, TrieTable t, float *MD, int32_t pitch, int32_t h0) {
-    const int lane = threadIdx.x & 31;
-    const int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= cnt) return;
-    const int32_t e = nodes[i];
+constexpr int kListThreads = 128;
+
+__global__ void __launch_bounds__(kListThreads) k_push_h2(const int64_t *__restrict__ out_off,
+                                                          const int32_t *__restrict__ out_col,
+                                                          const float *__restrict__ w, const int32_t *__restrict__ nodes,
+                                                          TrieTable t, float *MD, ColLayout L, int32_t h0) {
+    const int32_t e = nodes[blockIdx.x];
     const int32_t p = t.parent[t.parent[e]];  // the height-2 node
     const int32_t sl = t.slot[p];
     if (sl < h0) return;
     const int32_t a = t.node[e];
     const float g = t.gamma[e];
     const int64_t beg = out_off[a], end = out_off[a + 1];
-    for (int64_t k = beg + lane; k < end; k += 32) {
+    float *col = MD + L.base(sl);
+    const int32_t rp = L.rpitch(sl);
+    for (int64_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
         const int32_t x = __ldg(out_col + k);
-        atomicAdd(MD + (int64_t)x * pitch + sl, __ldg(w + x) * g);
+        atomicAdd(col + (int64_t)x * rp, __ldg(w + x) * g);
     }
 }
 
-void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, int32_t pitch,
+void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, ColLayout L,
                     int32_t h0, cudaStream_t s) {
     if (cnt <= 0) return;
-    const int64_t threads = (int64_t)cnt * 32;
-    k_push_h2<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(g.out_off, g.out_col, g.w, nodes, cnt, t, MD, pitch, h0);
+    k_push_h2<<<(unsigned)cnt, kListThreads, 0, s>>>(g.out_off, g.out_col, g.w, nodes, t, MD, L, h0);
 }
 
 // ------------------------------------------------------------------------------------------------
 // accumulate: D of the dense nodes of a depth, in place in the previous level's MD buffer.  A dense node's
 // column already holds its heir's MD (the heir inherits the column); each group g adds (or, for a node
 // without heir, sets) the sum of its other children's columns: B[v][dst_g] (+)= sum of B[v][src], src in
-// srcs[off_g .. off_g+1).  One warp per row: every group's sum is formed before any column is written, so a
-// column that is both a source and a later destination is read first.
+// srcs[off_g .. off_g+1).  No destination is a source of any group (the column assignment guarantees it), so
+// the groups are independent.  The groups touch most columns of every row, so the kernel streams rows
+// through shared memory: blocks of R rows are copied in with cp.async (the next block streams in while the
+// current one is updated), the destinations are updated there and the rows written back.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_accumulate(int32_t n, float *B, int32_t pitch, const int32_t *__restrict__ gdst,
-                                                    const int32_t *__restrict__ goff, const int32_t *__restrict__ srcs,
-                                                    int32_t ngroups) {
-    extern __shared__ float acc_sm[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *mine = acc_sm + (size_t)wib * ngroups;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp; v < n; v += nwarps) {
-        float *row = B + v * pitch;
-        for (int32_t gi = lane; gi < ngroups; gi += 32) {
-            float sum = 0.f;
-            const int32_t e = __ldg(goff + gi + 1);
-            for (int32_t k = __ldg(goff + gi); k < e; ++k) sum += row[__ldg(srcs + k)];
-            mine[gi] = sum;
+constexpr int kAccThreads = 256;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory stage of R rows, segment-major: segment k (columns [256k, 256k + 256) of a grouped layout,
+// or all pitch columns of a node-major one) holds the R rows one after another, exactly as they lie in
+// global memory, so staging and write-back are linear copies.  Column c of row r sits at
+// cbase(c) + r * segw.
+struct AccStage {
+    int32_t nseg, segw, R;
+    bool grouped;
+    __device__ int32_t cbase(int32_t c) const {
+        return grouped ? (((c >> 8) * R) << 8) + (c & (kGroup - 1)) : c;  // kGroup = 256
+    }
+};
+static_assert(kGroup == 256, "AccStage::cbase assumes 256-column groups");
+
+__global__ void __launch_bounds__(kAccThreads) k_accumulate(int32_t n, float *B, ColLayout L, int32_t wstore,
+                                                            const int32_t *__restrict__ gdst,
+                                                            const int32_t *__restrict__ goff,
+                                                            const int32_t *__restrict__ srcs, int32_t ngroups,
+                                                            int32_t R) {
+    extern __shared__ float4 acc_sm4[];
+    const AccStage S{L.K > 0 ? L.K : 1, L.K > 0 ? kGroup : L.R, R, L.K > 0};
+    const int32_t stage_floats = S.nseg * S.segw * R;
+    const int32_t wseg = L.K > 0 ? (wstore + kGroup - 1) / kGroup : 1;  // segments written back
+    const int64_t step = (int64_t)gridDim.x * R;
+    // issue the copies of rows [r0, r0 + nr) into stage buffer `buf`
+    auto stage_in = [&](float *buf, int64_t r0, int32_t nr) {
+        const int32_t q4 = nr * S.segw / 4;
+        for (int32_t k = 0; k < S.nseg; ++k) {
+            const float4 *src = reinterpret_cast<const float4 *>(B + L.at(r0, k * S.segw));
+            float4 *dst = reinterpret_cast<float4 *>(buf + k * R * S.segw);
+            for (int32_t i = threadIdx.x; i < q4; i += blockDim.x) cp_async16(dst + i, src + i);
         }
-        __syncwarp();
-        for (int32_t gi = lane; gi < ngroups; gi += 32) {
-            const int32_t d = __ldg(gdst + gi);
-            const int32_t c = d & 0x3fffffff;
-            row[c] = (d & (1 << 30)) ? mine[gi] : row[c] + mine[gi];  // bit 30: set (no heir)
+        cp_async_commit();
+    };
+    float *const sm = reinterpret_cast<float *>(acc_sm4);
+    int64_t r0 = (int64_t)blockIdx.x * R;
+    int32_t cur = 0;
+    if (r0 < n) stage_in(sm, r0, (int32_t)min((int64_t)R, (int64_t)n - r0));
+    for (; r0 < n; r0 += step, cur ^= 1) {
+        float *buf = sm + cur * stage_floats;
+        const int32_t nr = (int32_t)min((int64_t)R, (int64_t)n - r0);
+        const int64_t r1 = r0 + step;
+        if (r1 < n) {  // the next block of rows streams in while this one is updated
+            stage_in(sm + (cur ^ 1) * stage_floats, r1, (int32_t)min((int64_t)R, (int64_t)n - r1));
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
-        __syncwarp();
+        __syncthreads();
+        // (group, row set) items: with fewer groups than threads, rsplit threads share a group's rows; each
+        // item holds its group's sources in registers across its rows
+        const int32_t rs = S.segw;  // row stride inside a segment
+        const int32_t rsplit = max(1, min(nr, (int32_t)blockDim.x / max(1, ngroups)));
+        for (int32_t it = threadIdx.x; it < ngroups * rsplit; it += blockDim.x) {
+            const int32_t gi = it % ngroups, part = it / ngroups;
+            const int32_t b = __ldg(goff + gi), e = __ldg(goff + gi + 1), dd = __ldg(gdst + gi);
+            const int32_t cd = S.cbase(dd & 0x3fffffff);
+            const bool set = (dd & (1 << 30)) != 0;  // no heir: the column is set, not added to
+            if (e - b <= 4) {
+                int32_t s4[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) s4[j] = b + j < e ? S.cbase(__ldg(srcs + b + j)) : -1;
+                for (int32_t r = part; r < nr; r += rsplit) {
+                    float sum = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (s4[j] >= 0) sum += buf[s4[j] + r * rs];
+                    float &dst = buf[cd + r * rs];
+                    dst = set ? sum : dst + sum;
+                }
+            } else {
+                for (int32_t r = part; r < nr; r += rsplit) {
+                    float sum = 0.f;
+                    for (int32_t k = b; k < e; ++k) sum += buf[S.cbase(__ldg(srcs + k)) + r * rs];
+                    float &dst = buf[cd + r * rs];
+                    dst = set ? sum : dst + sum;
+                }
+            }
+        }
+        __syncthreads();
+        // write back the segments that can have changed (all of a node-major row block)
+        const int32_t q4 = nr * S.segw / 4;
+        for (int32_t k = 0; k < wseg; ++k) {
+            float4 *dst = reinterpret_cast<float4 *>(B + L.at(r0, k * S.segw));
+            const float4 *src = reinterpret_cast<const float4 *>(buf + k * R * S.segw);
+            for (int32_t i = threadIdx.x; i < q4; i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();  // the copies of a later iteration overwrite this buffer
     }
 }
 
-void launch_accumulate(int32_t n, float *B, int32_t pitch, const int32_t *gdst, const int32_t *goff, const int32_t *srcs,
-                       int32_t ngroups, cudaStream_t s) {
+// The same update straight in global memory, for rows too wide to stage (batches of many queries): one warp
+// per row, lanes over the groups.
+__global__ void __launch_bounds__(256) k_accumulate_direct(int32_t n, float *B, ColLayout L,
+                                                           const int32_t *__restrict__ gdst,
+                                                           const int32_t *__restrict__ goff,
+                                                           const int32_t *__restrict__ srcs, int32_t ngroups) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        for (int32_t gi = lane; gi < ngroups; gi += 32) {
+            float sum = 0.f;
+            const int32_t e = __ldg(goff + gi + 1);
+            for (int32_t k = __ldg(goff + gi); k < e; ++k) sum += B[L.at(v, __ldg(srcs + k))];
+            const int32_t d = __ldg(gdst + gi);
+            float *dst = B + L.at(v, d & 0x3fffffff);
+            *dst = (d & (1 << 30)) ? sum : *dst + sum;
+        }
+    }
+}
+
+void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *gdst, const int32_t *goff,
+                       const int32_t *srcs, int32_t ngroups, cudaStream_t s) {
     if (ngroups <= 0) return;
-    int warps = 8;
-    while (warps > 1 && (size_t)warps * ngroups * 4 > 96 * 1024) warps >>= 1;
-    const size_t smem = (size_t)warps * ngroups * 4;
+    const int32_t pitch = L.K > 0 ? L.K * kGroup : L.R;  // staged row width (a multiple of 4)
+    if ((size_t)pitch * sizeof(float) > 96 * 1024) {
+        k_accumulate_direct<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(n, B, L, gdst, goff, srcs, ngroups);
+        return;
+    }
+    // rows per stage: about 32 KB of rows, at least one (a row of up to 96 KB); two stages per block
+    const int32_t R = std::max<int32_t>(1, std::min<int32_t>(256, 8192 / std::max(1, pitch)));
+    const size_t smem = 2 * sizeof(float) * (size_t)R * pitch;
+    const int32_t wstore = std::min(pitch, (wdense + 3) / 4 * 4);
     cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    const int threads = warps * 32;
-    const int blocks = grid_for((int64_t)n * 32, threads, 2048 / threads);
-    k_accumulate<<<blocks, threads, smem, s>>>(n, B, pitch, gdst, goff, srcs, ngroups);
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / std::max<size_t>(1, smem)));
+    const int blocks = grid_for((int64_t)(n + R - 1) / R * kAccThreads, kAccThreads, per_sm);
+    k_accumulate<<<blocks, kAccThreads, smem, s>>>(n, B, L, wstore, gdst, goff, srcs, ngroups, R);
 }
 
 // ------------------------------------------------------------------------------------------------
 // Rows of vertices whose in-list is cut into several pieces receive atomic adds: zero them first.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_zero_rows(const int32_t *__restrict__ rows, int32_t cnt, float *MD, int32_t pitch, int32_t width) {
+__global__ void k_zero_rows(const int32_t *__restrict__ rows, int32_t cnt, float *MD, ColLayout L, int32_t width) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)cnt * width;
     if (i >= total) return;
-    const int64_t r = i / width, c = i - r * width;
-    MD[(int64_t)rows[r] * pitch + c] = 0.f;
+    const int64_t r = i / width;
+    const int32_t c = (int32_t)(i - r * width);
+    MD[L.at(rows[r], c)] = 0.f;
 }
 
-void launch_zero_split_rows(const DeviceGraph &g, float *MD, int32_t pitch, int32_t width, cudaStream_t s) {
+void launch_zero_split_rows(const DeviceGraph &g, float *MD, ColLayout L, int32_t width, cudaStream_t s) {
     const int64_t total = (int64_t)g.n_split * width;
     if (total <= 0) return;
-    k_zero_rows<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g.split_v, g.n_split, MD, pitch, width);
+    k_zero_rows<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g.split_v, g.n_split, MD, L, width);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
                                               const int32_t *__restrict__ piece_len, int64_t n_pieces,
                                               const int32_t *__restrict__ in_col, const float *__restrict__ w,
                                               const float *__restrict__ D, int32_t dpitch, float *__restrict__ MD,
-                                              int32_t pitch) {
+                                              int32_t pitch, int64_t dts, int32_t dsub, int64_t mts, int32_t msub) {
     constexpr int VEC = T >= 4 ? 4 : T;
     constexpr int L = T / VEC;         // lanes per group
     constexpr int CH = 8;              // in-neighbours per chunk
@@ -330,7 +333,8 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
     const int lane = threadIdx.x & 31;
     const int lig = lane % L;
     const unsigned gmask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (lane - lig));
-    const int32_t col0 = blockIdx.y * T + lig * VEC;
+    const int64_t dcol0 = (int64_t)(blockIdx.y / dsub) * dts + (blockIdx.y % dsub) * T + lig * VEC;
+    const int64_t mcol0 = (int64_t)(blockIdx.y / msub) * mts + (blockIdx.y % msub) * T + lig * VEC;
     const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L;
     const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / L;
     // Software pipeline over this group's pieces p, p + ngroups, ...: the metadata of the piece after next and
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
 #pragma unroll
             for (int j = 0; j < CH; ++j) {
                 const int32_t x = L == 1 ? mine[j] : __shfl_sync(gmask, mine[j / L], j % L, L);
-                val[j] = x >= 0 ? VecT<VEC>::load(D + (int64_t)x * dpitch + col0) : vzero<V>();
+                val[j] = x >= 0 ? VecT<VEC>::load(D + (int64_t)x * dpitch + dcol0) : vzero<V>();
             }
             e0 += CH;
             const bool more = e0 < len;
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
             if (!more) break;
         }
         const V res = vscale(acc, wv);
-        float *dst = MD + (int64_t)v * pitch + col0;
+        float *dst = MD + (int64_t)v * pitch + mcol0;
         if (info < 0) vatomic(dst, res); else vstore(dst, res);
         v = v1, beg = beg1, info = info1;
         v1 = v2, beg1 = beg2, info1 = info2;
@@ -398,21 +402,25 @@ int32_t pull_tile_for(int32_t S, int32_t wide) {
     return 32;
 }
 
-void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, float *MD, int32_t pitch, int32_t width,
-                 int32_t tile, int32_t blocks_per_sm, cudaStream_t s) {
-    const int32_t ntiles = width / tile;
+void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t dts, int32_t dsub, float *MD,
+                 int32_t pitch, int64_t mts, int32_t msub, int32_t ntiles, int32_t tile, int32_t blocks_per_sm,
+                 cudaStream_t s) {
+    if (ntiles <= 0) return;
     const int L = tile >= 4 ? tile / 4 : 1;
     const int64_t threads_needed = g.n_pieces * L;
     const int blocks = grid_for(threads_needed, 256, blocks_per_sm > 0 ? blocks_per_sm : 8);
     dim3 grid(blocks, ntiles);
+#define PS_PULL(T) k_pull<T><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, \
+                                                  dpitch, MD, pitch, dts, dsub, mts, msub)
     switch (tile) {
-        case 1: k_pull<1><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
-        case 2: k_pull<2><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
-        case 4: k_pull<4><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
-        case 8: k_pull<8><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
-        case 16: k_pull<16><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
-        default: k_pull<32><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, dpitch, MD, pitch); break;
+        case 1: PS_PULL(1); break;
+        case 2: PS_PULL(2); break;
+        case 4: PS_PULL(4); break;
+        case 8: PS_PULL(8); break;
+        case 16: PS_PULL(16); break;
+        default: PS_PULL(32); break;
     }
+#undef PS_PULL
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -420,24 +428,41 @@ void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, float *MD
 //   beta_t  = sqrt(c)/|I(a_t)| * (sum_{x in I(a_t)} MD(t)[x] + G_t)   (the score PROBE would give a_t)
 //   gamma_t = w_t / n_r - beta_t;  G_parent += gamma_t
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gamma(const int64_t *__restrict__ in_off, const int32_t *__restrict__ in_col,
-                                               const float *__restrict__ w, const int32_t *__restrict__ nodes,
-                                               int32_t cnt, TrieTable t, const float *__restrict__ inv_nr,
-                                               const float *__restrict__ MD, int32_t pc) {
-    const int lane = threadIdx.x & 31;
-    const int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= cnt) return;
-    const int32_t e = nodes[i];
+// One block per tree node (the in-list of a hub is long); four independent gathers per thread in flight.
+__global__ void __launch_bounds__(kListThreads) k_gamma(const int64_t *__restrict__ in_off,
+                                                        const int32_t *__restrict__ in_col,
+                                                        const float *__restrict__ w, const int32_t *__restrict__ nodes,
+                                                        TrieTable t, const float *__restrict__ inv_nr,
+                                                        const float *__restrict__ MD, ColLayout Lc) {
+    __shared__ float part[kListThreads / 32];
+    const int32_t e = nodes[blockIdx.x];
     const int32_t a = t.node[e];
     const int32_t sl = t.slot[e];
     float sum = 0.f;
     if (sl >= 0 && MD != nullptr) {
         const int64_t beg = in_off[a], end = in_off[a + 1];
-        for (int64_t k = beg + lane; k < end; k += 32) sum += __ldg(MD + (int64_t)__ldg(in_col + k) * pc + sl);
+        const float *col = MD + Lc.base(sl);
+        const int32_t rp = Lc.rpitch(sl);
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int64_t k = beg + threadIdx.x;
+        for (; k + 3 * kListThreads < end; k += 4 * kListThreads) {
+            const int32_t x0 = __ldg(in_col + k), x1 = __ldg(in_col + k + kListThreads);
+            const int32_t x2 = __ldg(in_col + k + 2 * kListThreads), x3 = __ldg(in_col + k + 3 * kListThreads);
+            sum += __ldg(col + (int64_t)x0 * rp);
+            s1 += __ldg(col + (int64_t)x1 * rp);
+            s2 += __ldg(col + (int64_t)x2 * rp);
+            s3 += __ldg(col + (int64_t)x3 * rp);
+        }
+        for (; k < end; k += kListThreads) sum += __ldg(col + (int64_t)__ldg(in_col + k) * rp);
+        sum += s1 + s2 + s3;
     }
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) {
-        const float beta = __ldg(w + a) * (sum + t.G[e]);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot = 0.f;
+        for (int i = 0; i < kListThreads / 32; ++i) tot += part[i];
+        const float beta = __ldg(w + a) * (tot + t.G[e]);
         const float g = (float)t.weight[e] * inv_nr[t.query[e]] - beta;
         t.gamma[e] = g;
         const int32_t p = t.parent[e];
@@ -446,31 +471,30 @@ __global__ void __launch_bounds__(256) k_gamma(const int64_t *__restrict__ in_of
 }
 
 void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, const float *inv_nr,
-                  const float *MD, int32_t pc, cudaStream_t s) {
+                  const float *MD, ColLayout L, cudaStream_t s) {
     if (cnt <= 0) return;
-    const int64_t threads = (int64_t)cnt * 32;
-    k_gamma<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(g.in_off, g.in_col, g.w, nodes, cnt, t, inv_nr, MD, pc);
+    k_gamma<<<(unsigned)cnt, kListThreads, 0, s>>>(g.in_off, g.in_col, g.w, nodes, t, inv_nr, MD, L);
 }
 
 // ------------------------------------------------------------------------------------------------
 // finalize: out[q][v] = MD0[ext2int[v]][rho_slot(q)] for the caller's node id v, out[q][u_q] = 1 (s(u,u) = 1).
 // ------------------------------------------------------------------------------------------------
 __global__ void k_finalize(int32_t n, int32_t B, const int32_t *__restrict__ qnode, const int32_t *__restrict__ rho_slot,
-                           const float *__restrict__ MD0, int32_t p0, const int32_t *__restrict__ ext2int,
+                           const float *__restrict__ MD0, ColLayout L, const int32_t *__restrict__ ext2int,
                            float *__restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int32_t q = blockIdx.y;
     if (i >= n) return;
     const int32_t sl = rho_slot[q];
-    float v = sl >= 0 ? MD0[(int64_t)ext2int[i] * p0 + sl] : 0.f;
+    float v = sl >= 0 ? MD0[L.at(ext2int[i], sl)] : 0.f;
     if ((int32_t)i == qnode[q]) v = 1.f;
     out[(int64_t)q * n + i] = v;
 }
 
 void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,
-                     int32_t p0, const int32_t *ext2int, float *out, cudaStream_t s) {
+                     ColLayout L, const int32_t *ext2int, float *out, cudaStream_t s) {
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)B);
-    k_finalize<<<grid, 256, 0, s>>>(n, B, qnode, rho_slot, MD0, p0, ext2int, out);
+    k_finalize<<<grid, 256, 0, s>>>(n, B, qnode, rho_slot, MD0, L, ext2int, out);
 }
 
 __global__ void k_map_ids(int32_t *ids, int64_t count, const int32_t *__restrict__ map) {

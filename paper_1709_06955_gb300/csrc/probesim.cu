@@ -403,21 +403,9 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     int32_t Dmax = 0;
     for (int32_t d = 0; d < D1; ++d)
         if (ncount[d] > 0) Dmax = d;
-    // per depth: tile of the pull, dense width dw (multiple of the tile), columns cols = dw + push columns,
-    // row pitch of MD (float4 rows when the tile is >= 4)
-    std::vector<int32_t> node_off(D1 + 1, 0), slot_off(D1 + 1, 0), pitch(D1, 0), tile(D1, 1), dw(D1, 0), cols(D1, 0);
-    int64_t maxpitch = 1, maxdw = 1;
-    for (int32_t d = 0; d < D1; ++d) {
-        node_off[d + 1] = node_off[d] + ncount[d];
-        tile[d] = pull_tile_for(std::max(1, scount[d]), g->tune_wide);
-        dw[d] = scount[d] > 0 ? round_up(scount[d], tile[d]) : 0;
-        cols[d] = dw[d] + hcount[d];
-        pitch[d] = cols[d] > 0 ? round_up(cols[d], std::min(4, tile[d])) : 0;  // rows aligned for the pull's vectors
-        slot_off[d + 1] = slot_off[d] + cols[d];
-        maxpitch = std::max<int64_t>(maxpitch, pitch[d]);
-        maxdw = std::max<int64_t>(maxdw, dw[d]);
-    }
-    const int32_t total_nodes = node_off[D1], S_total = slot_off[D1];
+    std::vector<int32_t> node_off(D1 + 1, 0), dw(D1, 0);
+    for (int32_t d = 0; d < D1; ++d) node_off[d + 1] = node_off[d] + ncount[d];
+    const int32_t total_nodes = node_off[D1];
     ws->stats.tree_nodes += total_nodes;
     for (int32_t d = 0; d < D1; ++d) ws->stats.vectors += scount[d] + hcount[d];
     PS_CUDA(ws->offs.ensure(sizeof(int32_t) * (D1 + 1)));
@@ -464,9 +452,9 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
             chain[pr] = std::max(chain[pr], chain[i] + 1);
         }
     // a chain is a maximal path of heirs; all its nodes share one column.  Chains are coloured deepest bottom
-    // first, each taking the smallest column whose chains all start below its bottom (every chain coloured
-    // before it ends at least as deep, so that is exactly "free over its depth range"); the columns in use at
-    // a depth then stay close to the number of dense nodes there.
+    // first, each taking the smallest column whose chains all start more than one depth below its bottom
+    // (every chain coloured before it ends at least as deep, so that is "free over its depth range and the
+    // depth below"); the columns in use at a depth then stay close to the number of dense nodes there.
     std::vector<char> is_heir(ncol_nodes, 0);
     for (int32_t i = 0; i < ncol_nodes; ++i)
         if (heir[i] >= 0) is_heir[heir[i]] = 1;
@@ -488,8 +476,10 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     });
     std::vector<int32_t> top_min;  // per column: the smallest top depth of the chains holding it
     for (const Chain &ch : chains) {
+        // a column whose chain ends at depth d stays unused at depth d+1 too: there the accumulate sets it to
+        // the chain bottom's D, while other groups may still read what a chain starting at d+1 left in it
         int32_t c = 0;
-        while (c < (int32_t)top_min.size() && top_min[c] <= ch.bottom) ++c;
+        while (c < (int32_t)top_min.size() && top_min[c] <= ch.bottom + 1) ++c;
         if (c == (int32_t)top_min.size()) top_min.push_back(ch.top);
         top_min[c] = std::min(top_min[c], ch.top);
         for (int32_t x = ch.head; x >= 0; x = heir[x]) col[x] = c;
@@ -505,26 +495,44 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         if (d == 0)
             for (int32_t i : dense_at[0]) rho[h_exp[5 * i + 4]] = col[i];
     }
-    for (int32_t d = 0; d <= Dmax; ++d) {  // pull tile and the width it covers
-        tile[d] = pull_tile_for(std::max(1, width[d]), g->tune_wide);
-        dw[d] = width[d] > 0 ? round_up(width[d], tile[d]) : 0;
+    // pull tiles per depth: full 32-column tiles (or 16-column halves, if the tuner prefers them) and one
+    // narrower tail tile of 1..16 columns; dw = the columns the pull covers
+    std::vector<int32_t> nfull(D1, 0), tail(D1, 0);
+    for (int32_t d = 0; d <= Dmax; ++d) {
+        int32_t full = width[d] / 32, rem = width[d] - 32 * full;
+        if (rem > 16) ++full, rem = 0;
+        nfull[d] = full;
+        tail[d] = rem > 0 ? pull_tile_for(rem, 16) : 0;
+        dw[d] = 32 * full + tail[d];
     }
-    // MD of depth d is read in place as D of depth d-1, so its rows must hold the columns of both depths:
-    // pitch(d) = max(dw[d-1], dw[d]) dense columns, then the push block of depth d at h0[d]
+    // MD of depth d is read in place as D of depth d-1, so its matrix holds the columns of both depths:
+    // max(dw[d-1], dw[d]) dense columns, then the push block of depth d at h0[d]
     std::vector<int32_t> h0v(D1, 0), rpv(D1, 0);
-    int64_t maxrp = 4;
+    std::vector<ColLayout> lay(D1);
+    int64_t max_floats = 4 * (int64_t)n;
     for (int32_t d = 0; d <= Dmax; ++d) {
         const int32_t dense_w = std::max(dw[d], d >= 1 ? dw[d - 1] : 0);
         h0v[d] = round_up(std::max(dense_w, 1), 4);
         rpv[d] = round_up(h0v[d] + (int32_t)push_at[d].size(), 4);
-        maxrp = std::max<int64_t>(maxrp, rpv[d]);
+        lay[d] = make_layout(n, rpv[d]);
+        max_floats = std::max<int64_t>(max_floats, lay[d].size());
+        ws->stats.max_columns = std::max<int64_t>(ws->stats.max_columns, rpv[d]);
     }
+    // push columns of a depth: grouped by parent (in parent column order), so a parent's push children are
+    // adjacent for the accumulate
     for (int32_t d = 0; d <= Dmax; ++d) {
         std::vector<int32_t> &pa = push_at[d];
-        std::sort(pa.begin(), pa.end(), [&](int32_t x, int32_t y) { return h_exp[5 * x] < h_exp[5 * y]; });
+        auto pcol = [&](int32_t x) {
+            const auto it = d >= 1 ? row_of.find(h_exp[5 * x + 2]) : row_of.end();
+            return it == row_of.end() ? -1 : col[it->second];
+        };
+        std::sort(pa.begin(), pa.end(), [&](int32_t x, int32_t y) {
+            const int32_t px = pcol(x), py = pcol(y);
+            return px != py ? px < py : h_exp[5 * x] < h_exp[5 * y];
+        });
         for (size_t r = 0; r < pa.size(); ++r) col[pa[r]] = h0v[d] + (int32_t)r;
     }
-    const size_t level_bytes2 = 2 * (size_t)maxrp * (size_t)n * sizeof(float);
+    const size_t level_bytes2 = 2 * (size_t)max_floats * sizeof(float);
     if (level_bytes2 > g->budget) {
         *too_big = B > 1;
         return fail(PROBESIM_E_NOMEM, "score vectors of one query exceed the workspace budget");
@@ -544,6 +552,10 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     }
     for (int32_t d = 0; d < D1; ++d) {
         goff_at[d] = (int32_t)gdst.size();
+        if (d <= Dmax) {  // groups in destination order, sources ascending
+            std::sort(dense_at[d].begin(), dense_at[d].end(), [&](int32_t x, int32_t y) { return col[x] < col[y]; });
+            for (int32_t i : dense_at[d]) std::sort(kids[i].begin(), kids[i].end());
+        }
         if (d <= Dmax)
             for (int32_t i : dense_at[d]) {
                 if (kids[i].empty() && heir[i] >= 0) continue;  // its column already is its heir's MD
@@ -573,32 +585,33 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     launch_set_slots(t, d_sched + o_pairs, (int32_t)(pairs.size() / 2), st);
     ++launches;
     const int32_t *d_rho = d_sched + o_rho;
-    // 4. level loop, deepest depth first.  Two MD buffers [n][P]: A receives this depth's MD; B holds the depth
+    // 4. level loop, deepest depth first.  Two score buffers: A receives this depth's MD; B holds the depth
     // below, which becomes this depth's D in place (accumulate + gamma scatter) before the pull reads it.
-    PS_CUDA(ws->md_a.ensure((size_t)n * (size_t)maxrp * sizeof(float)));
-    PS_CUDA(ws->md_b.ensure((size_t)n * (size_t)maxrp * sizeof(float)));
+    PS_CUDA(ws->md_a.ensure((size_t)max_floats * sizeof(float)));
+    PS_CUDA(ws->md_b.ensure((size_t)max_floats * sizeof(float)));
     float *A = ws->md_a.as<float>(), *Bm = ws->md_b.as<float>();
     const int32_t *node_list = ws->node_list.as<int32_t>();
+    const int32_t wide = g->tune_wide == 16 ? 16 : 32;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks;
     for (int32_t d = Dmax; d >= 0; --d) {
-        const int32_t S = scount[d], H = hcount[d], wd = dw[d];
-        const int32_t rp = rpv[d], rb = d + 1 <= Dmax ? rpv[d + 1] : 4, h0 = h0v[d], hb = d + 1 <= Dmax ? h0v[d + 1] : 0;
+        const int32_t S = scount[d], H = hcount[d];
+        const ColLayout La = lay[d], Lb = d + 1 <= Dmax ? lay[d + 1] : make_layout(n, 4);
         if (S > 0) {
             ph.begin(2);  // D of this depth's dense nodes, in place in B (the MD of depth d+1)
             if (gcount[d] > 0)
-                launch_accumulate(n, Bm, rb, d_sched + o_gdst + goff_at[d], d_sched + o_goff + goff_at[d],
+                launch_accumulate(n, Bm, Lb, dw[d], d_sched + o_gdst + goff_at[d], d_sched + o_goff + goff_at[d],
                                   d_sched + o_srcs, gcount[d], st);
             ph.end();
             ++launches;
             if (d + 2 <= Dmax) {
                 ph.begin(3);
-                launch_scatter_gamma(node_list + node_off[d + 2], ncount[d + 2], t, Bm, rb, hb > 0 ? hb : rb, st);
+                launch_scatter_gamma(node_list + node_off[d + 2], ncount[d + 2], t, Bm, Lb, h0v[d], st);
                 ph.end();
                 ++launches;
             }
             if (dg.n_split > 0) {
                 ph.begin(4);
-                launch_zero_split_rows(dg, A, rp, wd, st);
+                launch_zero_split_rows(dg, A, La, dw[d], st);
                 ph.end();
                 ++launches;
             }
@@ -608,8 +621,18 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
                 e1 = tm.get();
                 PS_CUDA(cudaEventRecord(e0, st));
             }
-            launch_pull(dg, Bm, rb, A, rp, wd, tile[d], g->tune_bps[tile[d]], st);
-            ++launches;
+            if (nfull[d] > 0) {  // 32-column tiles (or their 16-column halves)
+                const int32_t nt = nfull[d] * (32 / wide);
+                launch_pull(dg, Bm, Lb.rpitch(0), Lb.tile_stride(), Lb.tile_sub(wide), A, La.rpitch(0), La.tile_stride(),
+                            La.tile_sub(wide), nt, wide, g->tune_bps[wide], st);
+                ++launches;
+            }
+            if (tail[d] > 0) {  // the tail tile lies inside one group (or row) of each layout
+                const int32_t c = 32 * nfull[d];
+                launch_pull(dg, Bm + Lb.base(c), Lb.rpitch(c), 0, 1 << 30, A + La.base(c), La.rpitch(c), 0, 1 << 30, 1,
+                            tail[d], g->tune_bps[tail[d]], st);
+                ++launches;
+            }
             if (ws->profiling) {
                 PS_CUDA(cudaEventRecord(e1, st));
                 marks.push_back({e0, e1});
@@ -620,14 +643,14 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         }
         if (H > 0) {  // height-2 columns: zero, then push from the grandchildren's gamma
             ph.begin(6);
-            launch_zero_cols(n, A, rp, h0, H, st);
-            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, A, rp, h0, st);
+            launch_zero_cols(n, A, La, h0v[d], H, st);
+            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, A, La, h0v[d], st);
             ph.end();
             launches += 2;
         }
         if (d >= 1) {
             ph.begin(7);
-            launch_gamma(dg, node_list + node_off[d], ncount[d], t, qb.inv_nr, (S + H) > 0 ? A : nullptr, rp, st);
+            launch_gamma(dg, node_list + node_off[d], ncount[d], t, qb.inv_nr, (S + H) > 0 ? A : nullptr, La, st);
             ph.end();
             ++launches;
         }
@@ -638,7 +661,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     (void)maxw;
     // 5. estimates: s(u, v) = MD(super-root)[v], s(u, u) = 1
     ph.begin(8);
-    launch_finalize(n, B, qb.node, d_rho, scount[0] > 0 ? MD0 : nullptr, rpv[0], dg.ext2int, d_out, st);
+    launch_finalize(n, B, qb.node, d_rho, scount[0] > 0 ? MD0 : nullptr, lay[0], dg.ext2int, d_out, st);
     ph.end();
     ++launches;
     PS_CUDA(cudaGetLastError());
@@ -1195,32 +1218,48 @@ probesim_status probesim_autotune(probesim_graph *g, void *stream) {
     PS_CUDA(ws->md_a.ensure((size_t)n * P * sizeof(float)));
     PS_CUDA(ws->md_b.ensure((size_t)n * P * sizeof(float)));
     PS_CUDA(cudaMemsetAsync(ws->md_a.p, 0x3c, (size_t)n * P * sizeof(float), st));  // any finite values
-    const int32_t tiles[] = {1, 2, 4, 8, 16, 32}, bpss[] = {2, 4, 8, 16};
+    const int32_t tiles[] = {1, 2, 4, 8, 16}, bpss[] = {2, 4, 8, 16};
     Timer tm{ws, st};
-    double per_col[33] = {0};
-    for (int32_t T : tiles) {
-        double best = 1e30;
-        int32_t best_bps = 8;
-        for (int32_t bps : bpss) {
-            float total = 0.f;
-            for (int rep = 0; rep < 4; ++rep) {
-                cudaEvent_t e0 = tm.get(), e1 = tm.get();
-                PS_CUDA(cudaEventRecord(e0, st));
-                launch_pull(dg, ws->md_a.as<float>(), T, ws->md_b.as<float>(), P, T, T, bps, st);
-                PS_CUDA(cudaEventRecord(e1, st));
-                PS_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep > 0) total += ms;  // the first run warms the caches
-            }
-            if (total < best) {
-                best = total;
-                best_bps = bps;
-            }
+    // times one configuration: three runs after a warm-up run, in ms
+    auto time_pull = [&](auto &&launch) -> float {
+        float total = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEvent_t e0 = tm.get(), e1 = tm.get();
+            cudaEventRecord(e0, st);
+            launch();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) total += ms;
         }
-        g->tune_bps[T] = best_bps;
-        per_col[T] = best / 3.0 / T;
+        return total;
+    };
+    float *Da = ws->md_a.as<float>(), *Mb = ws->md_b.as<float>();
+    // tail tiles: one narrow tile over a compact [n][T] block
+    for (int32_t T : tiles) {
+        float best = 1e30f;
+        for (int32_t bps : bpss) {
+            const float ms = time_pull([&] { launch_pull(dg, Da, T, 0, 1, Mb, T, 0, 1, 1, T, bps, st); });
+            if (ms < best) best = ms, g->tune_bps[T] = bps;
+        }
     }
+    // wide tiles: two 32-column tiles of a node-major [n][64] matrix, as 32-column tiles or 16-column halves
+    double per_col[33] = {0};
+    int32_t wide_bps[33] = {0};
+    for (int32_t T : {16, 32}) {
+        float best = 1e30f;
+        for (int32_t bps : bpss) {
+            const int32_t nt = 2 * (32 / T);
+            const float ms =
+                time_pull([&] { launch_pull(dg, Da, P, 0, 1 << 30, Mb, P, 0, 1 << 30, nt, T, bps, st); });
+            if (ms < best) best = ms, wide_bps[T] = bps;
+        }
+        per_col[T] = best / 3.0 / 64.0;
+    }
+    PS_CUDA(cudaGetLastError());
+    g->tune_bps[32] = wide_bps[32];
+    if (per_col[16] < per_col[32]) g->tune_bps[16] = wide_bps[16];
     g->tune_wide = per_col[16] < per_col[32] ? 16 : 32;
     g->tuned = 1;
     PS_CUDA(cudaGetLastError());

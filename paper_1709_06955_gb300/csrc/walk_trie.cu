@@ -153,38 +153,6 @@ void launch_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, int32_t *
     k_sched_count<<<(unsigned)((t.cap + 255) / 256), 256, 0, s>>>(t, ncount, scount, hcount);
 }
 
-// Node lists per depth, push columns placed after the dense width dw[d], the column -> tree-node map, the
-// child counts of every column (a column's parent always has a dense column), and each query's super-root.
-__global__ void k_sched_lists(TrieTable t, const int32_t *__restrict__ node_off, const int32_t *__restrict__ slot_off,
-                              const int32_t *__restrict__ dw, int32_t *ncur, int32_t *node_list, int32_t *slot_entry,
-                              int32_t *nchild, int32_t *rho_slot) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= t.cap) return;
-    if (t.key[e] == kEmptyKey) return;
-    const int32_t d = t.depth[e];
-    node_list[node_off[d] + atomicAdd(&ncur[d], 1)] = (int32_t)e;
-    int32_t sl = t.slot[e];
-    if (sl <= -2) {
-        sl = dw[d] + (-2 - sl);
-        t.slot[e] = sl;
-    }
-    if (sl >= 0) {
-        slot_entry[slot_off[d] + sl] = (int32_t)e;
-        const int32_t p = t.parent[e];
-        if (p >= 0) {
-            int32_t ps = t.slot[p];  // dense (>= 0) by height; read before any rewrite could matter
-            atomicAdd(&nchild[slot_off[d - 1] + ps], 1);
-        }
-    }
-    if (d == 0) rho_slot[t.query[e]] = sl;
-}
-
-void launch_sched_lists(TrieTable t, const int32_t *node_off, const int32_t *slot_off, const int32_t *dw, int32_t *ncur,
-                        int32_t *node_list, int32_t *slot_entry, int32_t *nchild, int32_t *rho_slot, cudaStream_t s) {
-    k_sched_lists<<<(unsigned)((t.cap + 255) / 256), 256, 0, s>>>(t, node_off, slot_off, dw, ncur, node_list, slot_entry,
-                                                                 nchild, rho_slot);
-}
-
 // Exports every node that owns a column (dense or push): entry, depth, parent entry, dense flag, query.
 __global__ void k_sched_export(TrieTable t, int32_t *out, int32_t *count) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -225,56 +193,6 @@ __global__ void k_set_slots(TrieTable t, const int32_t *__restrict__ pairs, int3
 
 void launch_set_slots(TrieTable t, const int32_t *pairs, int32_t count, cudaStream_t s) {
     if (count > 0) k_set_slots<<<(count + 255) / 256, 256, 0, s>>>(t, pairs, count);
-}
-
-// Single-block exclusive scan: out[0..count] with out[count] = total.
-__global__ void __launch_bounds__(1024) k_scan_exclusive(const int32_t *__restrict__ in, int32_t *__restrict__ out,
-                                                         int32_t count) {
-    __shared__ int32_t s_part[1024];
-    const int32_t tid = threadIdx.x;
-    const int32_t per = (count + 1023) / 1024;
-    const int32_t beg = min(count, tid * per), end = min(count, beg + per);
-    int32_t local = 0;
-    for (int32_t i = beg; i < end; ++i) local += in[i];
-    s_part[tid] = local;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int32_t v = tid >= off ? s_part[tid - off] : 0;
-        __syncthreads();
-        s_part[tid] += v;
-        __syncthreads();
-    }
-    int32_t run = s_part[tid] - local;
-    for (int32_t i = beg; i < end; ++i) {
-        out[i] = run;
-        run += in[i];
-    }
-    if (tid == 1023) out[count] = s_part[1023];
-}
-
-void launch_scan_exclusive(const int32_t *in, int32_t *out, int32_t count, cudaStream_t s) {
-    k_scan_exclusive<<<1, 1024, 0, s>>>(in, out, count);
-}
-
-__global__ void k_sched_children(TrieTable t, const int32_t *__restrict__ slot_entry, int32_t S_total,
-                                 const int32_t *__restrict__ slot_off, const int32_t *__restrict__ child_off,
-                                 int32_t *ccur, int32_t *child_list) {
-    const int32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= S_total) return;
-    const int32_t e = slot_entry[gid];
-    if (e < 0) return;  // padding column
-    const int32_t p = t.parent[e];
-    if (p < 0) return;
-    const int32_t d = t.depth[e];
-    const int32_t pg = slot_off[d - 1] + t.slot[p];
-    child_list[child_off[pg] + atomicAdd(&ccur[pg], 1)] = t.slot[e];
-}
-
-void launch_sched_children(TrieTable t, const int32_t *slot_entry, int32_t S_total, const int32_t *slot_off,
-                           const int32_t *child_off, int32_t *ccur, int32_t *child_list, cudaStream_t s) {
-    if (S_total <= 0) return;
-    k_sched_children<<<(S_total + 255) / 256, 256, 0, s>>>(t, slot_entry, S_total, slot_off, child_off, ccur,
-                                                          child_list);
 }
 
 }  // namespace ps

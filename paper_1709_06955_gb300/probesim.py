@@ -39,9 +39,9 @@ class Stats(C.Structure):
     _fields_ = [("walks", C.c_int64), ("walk_nodes", C.c_int64), ("tree_nodes", C.c_int64), ("vectors", C.c_int64),
                 ("levels", C.c_int64), ("edge_gathers", C.c_int64), ("probe_launches", C.c_int64),
                 ("probe_ms", C.c_double), ("probe_bytes", C.c_double), ("kernel_launches", C.c_int64),
-                ("phase_ms", C.c_double * 12)]
+                ("phase_ms", C.c_double * 12), ("max_columns", C.c_int64)]
 
-    PHASES = ["walks", "tree", "dbuild", "scatter", "zero_rows", "pull", "push", "gamma", "estimates"]
+    PHASES = ["walks", "tree", "accumulate", "scatter", "zero_rows", "pull", "push", "gamma", "estimates"]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
