@@ -163,6 +163,7 @@ void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, Tri
 // wdense: the destinations are columns < wdense
 void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *gdst, const int32_t *goff,
                        const int32_t *srcs, int32_t ngroups, cudaStream_t s);
+// zeroes columns [c0, c0 + width) rounded up to a multiple of 4 (c0 a multiple of 4, inside the pitch)
 void launch_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width, cudaStream_t s);
 void launch_zero_split_rows(const DeviceGraph &g, float *MD, ColLayout L, int32_t width, cudaStream_t s);
 // pull MD[v][c] = w[v] * sum_{x in I(v)} D[x][c] over ntiles tiles of `tile` columns.  D and MD point at the

@@ -38,20 +38,23 @@ static int grid_for(int64_t work, int threads, int per_sm) {
     return (int)(blocks < 1 ? 1 : blocks);
 }
 
-// zero columns [c0, c0 + width) of every row; consecutive threads take consecutive columns of a row
-__global__ void k_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width) {
-    const int64_t total = (int64_t)n * width;
+// zero columns [c0, c0 + w4 * 4) of every row (c0 a multiple of 4), one float4 per thread; consecutive
+// threads take consecutive float4s of a row
+__global__ void k_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t w4) {
+    const int64_t total = (int64_t)n * w4;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = i / width;
-        const int32_t c = c0 + (int32_t)(i - v * width);
-        MD[L.at(v, c)] = 0.f;
+        const int64_t v = i / w4;
+        const int32_t c = c0 + 4 * (int32_t)(i - v * w4);
+        *reinterpret_cast<float4 *>(MD + L.at(v, c)) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
+// zeroes columns [c0, c0 + width) and up to the next multiple of 4 (padding of the push block)
 void launch_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width, cudaStream_t s) {
     if (width <= 0) return;
-    const int blocks = grid_for((int64_t)n * width, 256, 8);
-    k_zero_cols<<<blocks, 256, 0, s>>>(n, MD, L, c0, width);
+    const int32_t w4 = (width + 3) / 4;
+    const int blocks = grid_for((int64_t)n * w4, 256, 8);
+    k_zero_cols<<<blocks, 256, 0, s>>>(n, MD, L, c0, w4);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -216,8 +219,8 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(int32_t n, float *B,
     }
 }
 
-// The same update straight in global memory, for rows too wide to stage (batches of many queries): one warp
-// per row, lanes over the groups.
+// The same update straight in global memory, for wide rows (batches of queries): one warp per row, lanes
+// over the groups.
 __global__ void __launch_bounds__(256) k_accumulate_direct(int32_t n, float *B, ColLayout L,
                                                            const int32_t *__restrict__ gdst,
                                                            const int32_t *__restrict__ goff,
@@ -241,11 +244,13 @@ void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const i
                        const int32_t *srcs, int32_t ngroups, cudaStream_t s) {
     if (ngroups <= 0) return;
     const int32_t pitch = L.K > 0 ? L.K * kGroup : L.R;  // staged row width (a multiple of 4)
-    if ((size_t)pitch * sizeof(float) > 96 * 1024) {
+    // staging pays when a stage holds a few rows to spread each group's set-up over; wider rows (batches of
+    // queries) go straight to global memory
+    if (pitch > 2048) {
         k_accumulate_direct<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(n, B, L, gdst, goff, srcs, ngroups);
         return;
     }
-    // rows per stage: about 32 KB of rows, at least one (a row of up to 96 KB); two stages per block
+    // rows per stage: about 32 KB of rows (4 at the widest staged pitch); two stages per block
     const int32_t R = std::max<int32_t>(1, std::min<int32_t>(256, 8192 / std::max(1, pitch)));
     const size_t smem = 2 * sizeof(float) * (size_t)R * pitch;
     const int32_t wstore = std::min(pitch, (wdense + 3) / 4 * 4);
@@ -298,9 +303,14 @@ struct VecT<4> {
     __device__ static float4 load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 };
 
+// packed FP32x2 adds (one instruction for two lanes of a vector; each element rounds as a scalar add would)
 __device__ __forceinline__ void vadd(float &a, float b) { a += b; }
-__device__ __forceinline__ void vadd(float2 &a, float2 b) { a.x += b.x; a.y += b.y; }
-__device__ __forceinline__ void vadd(float4 &a, float4 b) { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
+__device__ __forceinline__ void vadd(float2 &a, float2 b) { a = __fadd2_rn(a, b); }
+__device__ __forceinline__ void vadd(float4 &a, float4 b) {
+    const float2 lo = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    const float2 hi = __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w));
+    a = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
 __device__ __forceinline__ float vscale(float a, float s) { return a * s; }
 __device__ __forceinline__ float2 vscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float4 vscale(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
