@@ -329,6 +329,18 @@ __device__ __forceinline__ void vstore(float *p, float v) { *p = v; }
 __device__ __forceinline__ void vstore(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 __device__ __forceinline__ void vstore(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
+// NCH row gathers of one chunk: in-neighbour j's index sits in lane j % L of the group, slot j / L; -1 (past the
+// end of the piece) gathers nothing
+template <int NCH, int L, int PER, class V, int VEC>
+__device__ __forceinline__ void pull_gather(const int32_t (&mine)[PER], unsigned gmask, const float *__restrict__ D,
+                                            int32_t dpitch, int64_t dcol0, V (&val)[NCH]) {
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+        const int32_t x = L == 1 ? mine[j] : __shfl_sync(gmask, mine[j / L], j % L, L);
+        val[j] = x >= 0 ? VecT<VEC>::load(D + (int64_t)x * dpitch + dcol0) : vzero<V>();
+    }
+}
+
 template <int T>
 __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const int32_t *__restrict__ piece_v, const int64_t *__restrict__ piece_beg,
                                               const int32_t *__restrict__ piece_len, int64_t n_pieces,
@@ -380,20 +392,20 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
         const float wv = __ldg(w + v);
         const int32_t len = info & 0x7fffffff;
         V acc = vzero<V>();
-        for (int32_t e0 = 0;;) {
-            V val[CH];
+        if (len == 0) {  // an empty in-list (about half the rows of a power-law graph): the row is zero
+            load_idx(beg1, info1 & 0x7fffffff, 0, mine);
+        } else {
+            for (int32_t e0 = 0;;) {
+                V val[CH];
+                pull_gather<CH, L, PER, V, VEC>(mine, gmask, D, dpitch, dcol0, val);
+                e0 += CH;
+                const bool more = e0 < len;
+                if (more) load_idx(beg, len, e0, mine);
+                else load_idx(beg1, info1 & 0x7fffffff, 0, mine);
 #pragma unroll
-            for (int j = 0; j < CH; ++j) {
-                const int32_t x = L == 1 ? mine[j] : __shfl_sync(gmask, mine[j / L], j % L, L);
-                val[j] = x >= 0 ? VecT<VEC>::load(D + (int64_t)x * dpitch + dcol0) : vzero<V>();
+                for (int j = 0; j < CH; ++j) vadd(acc, val[j]);
+                if (!more) break;
             }
-            e0 += CH;
-            const bool more = e0 < len;
-            if (more) load_idx(beg, len, e0, mine);
-            else load_idx(beg1, info1 & 0x7fffffff, 0, mine);
-#pragma unroll
-            for (int j = 0; j < CH; ++j) vadd(acc, val[j]);
-            if (!more) break;
         }
         const V res = vscale(acc, wv);
         float *dst = MD + (int64_t)v * pitch + mcol0;
