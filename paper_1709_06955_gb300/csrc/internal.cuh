@@ -111,8 +111,10 @@ struct LaunchCounters {
 // few cache lines, so equal rows of different groups do not map to the same memory partition).  A pull
 // tile of 32 columns then gathers 128 B per row from inside one block of n KB whatever the total width,
 // while the kernels that touch many columns of one row (accumulate, gamma) still find them in one row.
+// Every layout has one spare row, row n: the pull pads the last chunk of an in-list with index n, and that
+// row is zeroed before each pull reads the matrix (launch_zero_spare_row).
 constexpr int32_t kGroup = 256;
-constexpr int64_t kGroupSkew = 5 * 32;  // floats: five 128-byte lines
+constexpr int64_t kGroupSkew = kGroup + 5 * 32;  // floats: the spare row, then five 128-byte lines
 
 struct ColLayout {
     int64_t n = 0;
@@ -126,7 +128,7 @@ struct ColLayout {
     __host__ __device__ int64_t at(int64_t v, int32_t c) const {
         return K > 0 ? (int64_t)(c / kGroup) * gs + v * kGroup + (c % kGroup) : v * R + c;
     }
-    __host__ __device__ int64_t size() const { return K > 0 ? (int64_t)K * gs : (int64_t)R * n; }
+    __host__ __device__ int64_t size() const { return K > 0 ? (int64_t)K * gs : (int64_t)R * (n + 1); }
     // a pull over consecutive tiles of T columns starting at column 0: tile j starts (j / sub) * ts + (j % sub)
     // * T floats after column 0
     int64_t tile_stride() const { return K > 0 ? gs : 0; }
@@ -166,9 +168,12 @@ void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const i
 // zeroes columns [c0, c0 + width) rounded up to a multiple of 4 (c0 a multiple of 4, inside the pitch)
 void launch_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width, cudaStream_t s);
 void launch_zero_split_rows(const DeviceGraph &g, float *MD, ColLayout L, int32_t width, cudaStream_t s);
+// zeroes columns [0, width) of the spare row n
+void launch_zero_spare_row(float *MD, ColLayout L, int32_t width, cudaStream_t s);
 // pull MD[v][c] = w[v] * sum_{x in I(v)} D[x][c] over ntiles tiles of `tile` columns.  D and MD point at the
 // first tile's column in row 0; their rows are dpitch / pitch floats apart; tile j of D starts (j / dsub) * dts +
 // (j % dsub) * tile floats after the first, and likewise for MD with mts / msub (ColLayout::tile_stride/sub).
+// Row n of D (the spare row) must be zero over the pulled columns.
 void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t dts, int32_t dsub, float *MD,
                  int32_t pitch, int64_t mts, int32_t msub, int32_t ntiles, int32_t tile, int32_t blocks_per_sm,
                  cudaStream_t s);

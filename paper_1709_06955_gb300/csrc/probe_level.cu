@@ -272,6 +272,16 @@ __global__ void k_zero_rows(const int32_t *__restrict__ rows, int32_t cnt, float
     MD[L.at(rows[r], c)] = 0.f;
 }
 
+__global__ void k_zero_spare_row(float *MD, ColLayout L, int32_t width) {
+    const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < width) MD[L.at(L.n, c)] = 0.f;
+}
+
+void launch_zero_spare_row(float *MD, ColLayout L, int32_t width, cudaStream_t s) {
+    if (width <= 0) return;
+    k_zero_spare_row<<<(width + 255) / 256, 256, 0, s>>>(MD, L, width);
+}
+
 void launch_zero_split_rows(const DeviceGraph &g, float *MD, ColLayout L, int32_t width, cudaStream_t s) {
     const int64_t total = (int64_t)g.n_split * width;
     if (total <= 0) return;
@@ -329,15 +339,15 @@ __device__ __forceinline__ void vstore(float *p, float v) { *p = v; }
 __device__ __forceinline__ void vstore(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 __device__ __forceinline__ void vstore(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
-// NCH row gathers of one chunk: in-neighbour j's index sits in lane j % L of the group, slot j / L; -1 (past the
-// end of the piece) gathers nothing
+// NCH row gathers of one chunk: in-neighbour j's index sits in lane j % L of the group, slot j / L; past the end
+// of the piece the index is n, the zero spare row
 template <int NCH, int L, int PER, class V, int VEC>
 __device__ __forceinline__ void pull_gather(const int32_t (&mine)[PER], unsigned gmask, const float *__restrict__ D,
                                             int32_t dpitch, int64_t dcol0, V (&val)[NCH]) {
 #pragma unroll
     for (int j = 0; j < NCH; ++j) {
         const int32_t x = L == 1 ? mine[j] : __shfl_sync(gmask, mine[j / L], j % L, L);
-        val[j] = x >= 0 ? VecT<VEC>::load(D + (int64_t)x * dpitch + dcol0) : vzero<V>();
+        val[j] = VecT<VEC>::load(D + (int64_t)x * dpitch + dcol0);
     }
 }
 
@@ -346,7 +356,8 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
                                               const int32_t *__restrict__ piece_len, int64_t n_pieces,
                                               const int32_t *__restrict__ in_col, const float *__restrict__ w,
                                               const float *__restrict__ D, int32_t dpitch, float *__restrict__ MD,
-                                              int32_t pitch, int64_t dts, int32_t dsub, int64_t mts, int32_t msub) {
+                                              int32_t pitch, int64_t dts, int32_t dsub, int64_t mts, int32_t msub,
+                                              int32_t zrow) {
     constexpr int VEC = T >= 4 ? 4 : T;
     constexpr int L = T / VEC;         // lanes per group
     constexpr int CH = 8;              // in-neighbours per chunk
@@ -375,7 +386,7 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
             const int32_t e = e0 + lig + L * r;
-            mine[r] = e < len ? __ldg(in_col + beg + e) : -1;
+            mine[r] = e < len ? __ldg(in_col + beg + e) : zrow;
         }
     };
     int64_t p = gid;
@@ -433,7 +444,7 @@ void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t d
     const int blocks = grid_for(threads_needed, 256, blocks_per_sm > 0 ? blocks_per_sm : 8);
     dim3 grid(blocks, ntiles);
 #define PS_PULL(T) k_pull<T><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, \
-                                                  dpitch, MD, pitch, dts, dsub, mts, msub)
+                                                  dpitch, MD, pitch, dts, dsub, mts, msub, g.n)
     switch (tile) {
         case 1: PS_PULL(1); break;
         case 2: PS_PULL(2); break;

@@ -615,6 +615,8 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
                 ph.end();
                 ++launches;
             }
+            launch_zero_spare_row(Bm, Lb, dw[d], st);  // the pull's padding gathers read it
+            ++launches;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (ws->profiling) {
                 e0 = tm.get();
@@ -1215,9 +1217,9 @@ probesim_status probesim_autotune(probesim_graph *g, void *stream) {
     const DeviceGraph &dg = g->dg;
     const int32_t n = dg.n, P = 64;
     Workspace *ws = &g->ws0;
-    PS_CUDA(ws->md_a.ensure((size_t)n * P * sizeof(float)));
-    PS_CUDA(ws->md_b.ensure((size_t)n * P * sizeof(float)));
-    PS_CUDA(cudaMemsetAsync(ws->md_a.p, 0x3c, (size_t)n * P * sizeof(float), st));  // any finite values
+    PS_CUDA(ws->md_a.ensure((size_t)(n + 1) * P * sizeof(float)));  // a spare row after the n rows
+    PS_CUDA(ws->md_b.ensure((size_t)(n + 1) * P * sizeof(float)));
+    PS_CUDA(cudaMemsetAsync(ws->md_a.p, 0x3c, (size_t)(n + 1) * P * sizeof(float), st));  // any finite values
     const int32_t tiles[] = {1, 2, 4, 8, 16}, bpss[] = {2, 4, 8, 16};
     Timer tm{ws, st};
     // times one configuration: three runs after a warm-up run, in ms
