@@ -71,6 +71,18 @@ struct Workspace {
     int profiling = 0;
     std::vector<cudaEvent_t> ev;
     probesim_stats stats{};
+    // a second stream for work of a depth that runs beside the pull (push columns, the tail tile), and the
+    // events that order it against the caller's stream; created on first use
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_ready = nullptr, ev_side = nullptr;
+    cudaError_t ensure_side() {
+        if (side) return cudaSuccess;
+        cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming);
+        return e;
+    }
     void release() {
         DevBuf *bufs[] = {&qbuf, &walks, &lens, &ctr, &t_key, &t_node, &t_parent, &t_depth, &t_query, &t_weight,
                           &t_height, &t_slot, &t_gamma, &t_G, &counts, &offs, &node_list, &slot_entry, &nchild,
@@ -83,6 +95,9 @@ struct Workspace {
         pin_s.release();
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         ev.clear();
+        for (cudaEvent_t *e : {&ev_start, &ev_ready, &ev_side})
+            if (*e) cudaEventDestroy(*e), *e = nullptr;
+        if (side) cudaStreamDestroy(side), side = nullptr;
     }
 };
 

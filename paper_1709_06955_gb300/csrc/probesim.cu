@@ -593,9 +593,27 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     const int32_t *node_list = ws->node_list.as<int32_t>();
     const int32_t wide = g->tune_wide == 16 ? 16 : 32;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks;
+    // Without profiling, the push columns and the tail tile of a depth run on a second stream beside the
+    // accumulate and the full-tile pull: they write other columns of A than the full tiles do.  With
+    // profiling everything stays on the caller's stream, so the phase times do not overlap.
+    const bool overlap = !ws->profiling;
+    if (overlap) PS_CUDA(ws->ensure_side());
+    cudaStream_t ss = overlap ? ws->side : st;
     for (int32_t d = Dmax; d >= 0; --d) {
         const int32_t S = scount[d], H = hcount[d];
         const ColLayout La = lay[d], Lb = d + 1 <= Dmax ? lay[d + 1] : make_layout(n, 4);
+        const bool side_work = H > 0 || (S > 0 && tail[d] > 0);
+        if (overlap && side_work) {  // side work of this depth starts after everything before it
+            PS_CUDA(cudaEventRecord(ws->ev_start, st));
+            PS_CUDA(cudaStreamWaitEvent(ss, ws->ev_start, 0));
+        }
+        if (H > 0) {  // height-2 columns: zero, then push from the grandchildren's gamma
+            ph.begin(6);
+            launch_zero_cols(n, A, La, h0v[d], H, ss);
+            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, A, La, h0v[d], ss);
+            ph.end();
+            launches += 2;
+        }
         if (S > 0) {
             ph.begin(2);  // D of this depth's dense nodes, in place in B (the MD of depth d+1)
             if (gcount[d] > 0)
@@ -609,13 +627,13 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
                 ph.end();
                 ++launches;
             }
+            ph.begin(4);
+            launch_zero_spare_row(Bm, Lb, dw[d], st);  // the pull's padding gathers read it
             if (dg.n_split > 0) {
-                ph.begin(4);
                 launch_zero_split_rows(dg, A, La, dw[d], st);
-                ph.end();
                 ++launches;
             }
-            launch_zero_spare_row(Bm, Lb, dw[d], st);  // the pull's padding gathers read it
+            ph.end();
             ++launches;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (ws->profiling) {
@@ -623,16 +641,20 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
                 e1 = tm.get();
                 PS_CUDA(cudaEventRecord(e0, st));
             }
+            if (tail[d] > 0) {  // the tail tile lies inside one group (or row) of each layout
+                if (overlap) {
+                    PS_CUDA(cudaEventRecord(ws->ev_ready, st));
+                    PS_CUDA(cudaStreamWaitEvent(ss, ws->ev_ready, 0));
+                }
+                const int32_t c = 32 * nfull[d];
+                launch_pull(dg, Bm + Lb.base(c), Lb.rpitch(c), 0, 1 << 30, A + La.base(c), La.rpitch(c), 0, 1 << 30, 1,
+                            tail[d], g->tune_bps[tail[d]], ss);
+                ++launches;
+            }
             if (nfull[d] > 0) {  // 32-column tiles (or their 16-column halves)
                 const int32_t nt = nfull[d] * (32 / wide);
                 launch_pull(dg, Bm, Lb.rpitch(0), Lb.tile_stride(), Lb.tile_sub(wide), A, La.rpitch(0), La.tile_stride(),
                             La.tile_sub(wide), nt, wide, g->tune_bps[wide], st);
-                ++launches;
-            }
-            if (tail[d] > 0) {  // the tail tile lies inside one group (or row) of each layout
-                const int32_t c = 32 * nfull[d];
-                launch_pull(dg, Bm + Lb.base(c), Lb.rpitch(c), 0, 1 << 30, A + La.base(c), La.rpitch(c), 0, 1 << 30, 1,
-                            tail[d], g->tune_bps[tail[d]], st);
                 ++launches;
             }
             if (ws->profiling) {
@@ -643,12 +665,9 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
             ws->stats.edge_gathers += dg.m * (int64_t)S;
             ws->stats.probe_bytes += 4.0 * dg.m + 16.0 * dg.n_pieces + 4.0 * n + 8.0 * (double)n * S;
         }
-        if (H > 0) {  // height-2 columns: zero, then push from the grandchildren's gamma
-            ph.begin(6);
-            launch_zero_cols(n, A, La, h0v[d], H, st);
-            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, A, La, h0v[d], st);
-            ph.end();
-            launches += 2;
+        if (overlap && side_work) {  // the gamma of this depth (and every later step) waits for the side work
+            PS_CUDA(cudaEventRecord(ws->ev_side, ss));
+            PS_CUDA(cudaStreamWaitEvent(st, ws->ev_side, 0));
         }
         if (d >= 1) {
             ph.begin(7);
