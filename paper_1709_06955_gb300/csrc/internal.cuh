@@ -162,9 +162,10 @@ void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float 
                           cudaStream_t s);
 void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, ColLayout L,
                     int32_t h0, cudaStream_t s);
-// wdense: the destinations are columns < wdense
-void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *gdst, const int32_t *goff,
-                       const int32_t *srcs, int32_t ngroups, cudaStream_t s);
+// Parts of at most four sources: p1 (the first part of every group: bit 30 of the destination = set, else add)
+// then p2 (later parts: add).  Sources are -1 where absent; the destinations are columns < wdense.
+void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *p1dst, const int4 *p1src,
+                       int32_t np1, const int32_t *p2dst, const int4 *p2src, int32_t np2, cudaStream_t s);
 // zeroes columns [c0, c0 + width) rounded up to a multiple of 4 (c0 a multiple of 4, inside the pitch)
 void launch_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width, cudaStream_t s);
 void launch_zero_split_rows(const DeviceGraph &g, float *MD, ColLayout L, int32_t width, cudaStream_t s);

@@ -142,11 +142,22 @@ struct AccStage {
 };
 static_assert(kGroup == 256, "AccStage::cbase assumes 256-column groups");
 
+// sum over a part's (at most four) sources of row r, and its destination column's address, inside a stage
+__device__ __forceinline__ float acc_part_sum(const float *buf, const AccStage &S, int4 sc, int32_t r) {
+    const int32_t rs = r * S.segw;
+    float sum = 0.f;
+    if (sc.x >= 0) sum += buf[S.cbase(sc.x) + rs];
+    if (sc.y >= 0) sum += buf[S.cbase(sc.y) + rs];
+    if (sc.z >= 0) sum += buf[S.cbase(sc.z) + rs];
+    if (sc.w >= 0) sum += buf[S.cbase(sc.w) + rs];
+    return sum;
+}
+
 __global__ void __launch_bounds__(kAccThreads) k_accumulate(int32_t n, float *B, ColLayout L, int32_t wstore,
-                                                            const int32_t *__restrict__ gdst,
-                                                            const int32_t *__restrict__ goff,
-                                                            const int32_t *__restrict__ srcs, int32_t ngroups,
-                                                            int32_t R) {
+                                                            const int32_t *__restrict__ p1dst,
+                                                            const int4 *__restrict__ p1src, int32_t np1,
+                                                            const int32_t *__restrict__ p2dst,
+                                                            const int4 *__restrict__ p2src, int32_t np2, int32_t R) {
     extern __shared__ float4 acc_sm4[];
     const AccStage S{L.K > 0 ? L.K : 1, L.K > 0 ? kGroup : L.R, R, L.K > 0};
     const int32_t stage_floats = S.nseg * S.segw * R;
@@ -177,34 +188,26 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(int32_t n, float *B,
             cp_async_wait<0>();
         }
         __syncthreads();
-        // (group, row set) items: with fewer groups than threads, rsplit threads share a group's rows; each
-        // item holds its group's sources in registers across its rows
-        const int32_t rs = S.segw;  // row stride inside a segment
-        const int32_t rsplit = max(1, min(nr, (int32_t)blockDim.x / max(1, ngroups)));
-        for (int32_t it = threadIdx.x; it < ngroups * rsplit; it += blockDim.x) {
-            const int32_t gi = it % ngroups, part = it / ngroups;
-            const int32_t b = __ldg(goff + gi), e = __ldg(goff + gi + 1), dd = __ldg(gdst + gi);
+        // first parts: (part, row set) items; with fewer parts than threads, rsplit threads share a part's rows
+        const int32_t rsplit = max(1, min(nr, (int32_t)blockDim.x / max(1, np1)));
+        for (int32_t it = threadIdx.x; it < np1 * rsplit; it += blockDim.x) {
+            const int32_t pi = it % np1, part = it / np1;
+            const int32_t dd = __ldg(p1dst + pi);
+            const int4 sc = __ldg(p1src + pi);
             const int32_t cd = S.cbase(dd & 0x3fffffff);
             const bool set = (dd & (1 << 30)) != 0;  // no heir: the column is set, not added to
-            if (e - b <= 4) {
-                int32_t s4[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) s4[j] = b + j < e ? S.cbase(__ldg(srcs + b + j)) : -1;
-                for (int32_t r = part; r < nr; r += rsplit) {
-                    float sum = 0.f;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (s4[j] >= 0) sum += buf[s4[j] + r * rs];
-                    float &dst = buf[cd + r * rs];
-                    dst = set ? sum : dst + sum;
-                }
-            } else {
-                for (int32_t r = part; r < nr; r += rsplit) {
-                    float sum = 0.f;
-                    for (int32_t k = b; k < e; ++k) sum += buf[S.cbase(__ldg(srcs + k)) + r * rs];
-                    float &dst = buf[cd + r * rs];
-                    dst = set ? sum : dst + sum;
-                }
+            for (int32_t r = part; r < nr; r += rsplit) {
+                const float sum = acc_part_sum(buf, S, sc, r);
+                float &dst = buf[cd + r * S.segw];
+                dst = set ? sum : dst + sum;
+            }
+        }
+        if (np2 > 0) {  // later parts of groups with more than four sources add atomically
+            __syncthreads();
+            for (int32_t it = threadIdx.x; it < np2 * nr; it += blockDim.x) {
+                const int32_t pi = it % np2, r = it / np2;
+                const int4 sc = __ldg(p2src + pi);
+                atomicAdd(buf + S.cbase(__ldg(p2dst + pi)) + r * S.segw, acc_part_sum(buf, S, sc, r));
             }
         }
         __syncthreads();
@@ -219,45 +222,60 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(int32_t n, float *B,
     }
 }
 
-// The same update straight in global memory, for wide rows (batches of queries): one warp per row, lanes
-// over the groups.
+// The same update straight in global memory, for wide rows: one warp per row, lanes over the parts; the
+// later parts add atomically after the first parts of the row are done.
+__device__ __forceinline__ float acc_part_sum_global(const float *B, const ColLayout &L, int64_t v, int4 sc) {
+    float sum = 0.f;
+    if (sc.x >= 0) sum += B[L.at(v, sc.x)];
+    if (sc.y >= 0) sum += B[L.at(v, sc.y)];
+    if (sc.z >= 0) sum += B[L.at(v, sc.z)];
+    if (sc.w >= 0) sum += B[L.at(v, sc.w)];
+    return sum;
+}
+
 __global__ void __launch_bounds__(256) k_accumulate_direct(int32_t n, float *B, ColLayout L,
-                                                           const int32_t *__restrict__ gdst,
-                                                           const int32_t *__restrict__ goff,
-                                                           const int32_t *__restrict__ srcs, int32_t ngroups) {
+                                                           const int32_t *__restrict__ p1dst,
+                                                           const int4 *__restrict__ p1src, int32_t np1,
+                                                           const int32_t *__restrict__ p2dst,
+                                                           const int4 *__restrict__ p2src, int32_t np2) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t v = warp; v < n; v += nwarps) {
-        for (int32_t gi = lane; gi < ngroups; gi += 32) {
-            float sum = 0.f;
-            const int32_t e = __ldg(goff + gi + 1);
-            for (int32_t k = __ldg(goff + gi); k < e; ++k) sum += B[L.at(v, __ldg(srcs + k))];
-            const int32_t d = __ldg(gdst + gi);
+        for (int32_t pi = lane; pi < np1; pi += 32) {
+            const float sum = acc_part_sum_global(B, L, v, __ldg(p1src + pi));
+            const int32_t d = __ldg(p1dst + pi);
             float *dst = B + L.at(v, d & 0x3fffffff);
             *dst = (d & (1 << 30)) ? sum : *dst + sum;
+        }
+        if (np2 > 0) {
+            __syncwarp();
+            for (int32_t pi = lane; pi < np2; pi += 32)
+                atomicAdd(B + L.at(v, __ldg(p2dst + pi)), acc_part_sum_global(B, L, v, __ldg(p2src + pi)));
+            __syncwarp();
         }
     }
 }
 
-void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *gdst, const int32_t *goff,
-                       const int32_t *srcs, int32_t ngroups, cudaStream_t s) {
-    if (ngroups <= 0) return;
+void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *p1dst, const int4 *p1src,
+                       int32_t np1, const int32_t *p2dst, const int4 *p2src, int32_t np2, cudaStream_t s) {
+    if (np1 <= 0) return;
     const int32_t pitch = L.K > 0 ? L.K * kGroup : L.R;  // staged row width (a multiple of 4)
-    // staging pays when a stage holds a few rows to spread each group's set-up over; wider rows (batches of
+    // staging pays when a stage holds a few rows to spread each part's set-up over; wider rows (batches of
     // queries) go straight to global memory
     if (pitch > 2048) {
-        k_accumulate_direct<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(n, B, L, gdst, goff, srcs, ngroups);
+        k_accumulate_direct<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(n, B, L, p1dst, p1src, np1, p2dst,
+                                                                             p2src, np2);
         return;
     }
-    // rows per stage: about 32 KB of rows (4 at the widest staged pitch); two stages per block
+    // rows per stage: about 32 KB of rows (at least 4); two stages per block
     const int32_t R = std::max<int32_t>(1, std::min<int32_t>(256, 8192 / std::max(1, pitch)));
     const size_t smem = 2 * sizeof(float) * (size_t)R * pitch;
     const int32_t wstore = std::min(pitch, (wdense + 3) / 4 * 4);
     cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / std::max<size_t>(1, smem)));
     const int blocks = grid_for((int64_t)(n + R - 1) / R * kAccThreads, kAccThreads, per_sm);
-    k_accumulate<<<blocks, kAccThreads, smem, s>>>(n, B, L, wstore, gdst, goff, srcs, ngroups, R);
+    k_accumulate<<<blocks, kAccThreads, smem, s>>>(n, B, L, wstore, p1dst, p1src, np1, p2dst, p2src, np2, R);
 }
 
 // ------------------------------------------------------------------------------------------------

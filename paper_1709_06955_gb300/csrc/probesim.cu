@@ -544,31 +544,38 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         const auto it = row_of.find(h_exp[5 * i + 2]);
         if (it != row_of.end() && heir[it->second] != i) kids[it->second].push_back(col[i]);
     }
-    std::vector<int32_t> pairs, gdst, goff, srcs, goff_at(D1 + 1, 0), gcount(D1, 0);
+    // Each group is cut into parts of at most four sources, stored as a destination (bit 30: set, for a node
+    // without heir) and an int4 of sources (-1 = none).  The first part of every group runs in the
+    // accumulate's first phase, the others add in a second phase (so one node with many children does not
+    // hold up a block).  Records of depth d: first parts [p1_at[d], p1_at[d+1]), later parts likewise.
+    std::vector<int32_t> pairs, p1dst, p1src, p2dst, p2src, p1_at(D1 + 1, 0), p2_at(D1 + 1, 0);
     pairs.reserve(2 * (size_t)ncol_nodes);
     for (int32_t i = 0; i < ncol_nodes; ++i) {
         pairs.push_back(h_exp[5 * i]);
         pairs.push_back(col[i]);
     }
+    auto put_part = [](std::vector<int32_t> &dst, std::vector<int32_t> &src, int32_t dcol, const std::vector<int32_t> &k,
+                       size_t from) {
+        dst.push_back(dcol);
+        for (size_t j = 0; j < 4; ++j) src.push_back(from + j < k.size() ? k[from + j] : -1);
+    };
     for (int32_t d = 0; d < D1; ++d) {
-        goff_at[d] = (int32_t)gdst.size();
-        if (d <= Dmax) {  // groups in destination order, sources ascending
-            std::sort(dense_at[d].begin(), dense_at[d].end(), [&](int32_t x, int32_t y) { return col[x] < col[y]; });
-            for (int32_t i : dense_at[d]) std::sort(kids[i].begin(), kids[i].end());
+        p1_at[d] = (int32_t)p1dst.size();
+        p2_at[d] = (int32_t)p2dst.size();
+        if (d > Dmax) continue;
+        // groups in destination order, sources ascending
+        std::sort(dense_at[d].begin(), dense_at[d].end(), [&](int32_t x, int32_t y) { return col[x] < col[y]; });
+        for (int32_t i : dense_at[d]) {
+            std::sort(kids[i].begin(), kids[i].end());
+            if (kids[i].empty() && heir[i] >= 0) continue;  // its column already is its heir's MD
+            put_part(p1dst, p1src, col[i] | (heir[i] < 0 ? (1 << 30) : 0), kids[i], 0);
+            for (size_t f = 4; f < kids[i].size(); f += 4) put_part(p2dst, p2src, col[i], kids[i], f);
         }
-        if (d <= Dmax)
-            for (int32_t i : dense_at[d]) {
-                if (kids[i].empty() && heir[i] >= 0) continue;  // its column already is its heir's MD
-                gdst.push_back(col[i] | (heir[i] < 0 ? (1 << 30) : 0));
-                goff.push_back((int32_t)srcs.size());
-                srcs.insert(srcs.end(), kids[i].begin(), kids[i].end());
-            }
-        gcount[d] = (int32_t)gdst.size() - goff_at[d];
     }
-    goff_at[D1] = (int32_t)gdst.size();
-    goff.push_back((int32_t)srcs.size());
-    // upload: slot pairs, group destinations, group offsets (global into srcs), sources, super-root columns
-    const size_t sched_ints = pairs.size() + gdst.size() + goff.size() + srcs.size() + B;
+    p1_at[D1] = (int32_t)p1dst.size();
+    p2_at[D1] = (int32_t)p2dst.size();
+    // upload: slot pairs, super-root columns, part destinations, part sources (int4, 16-byte aligned)
+    const size_t sched_ints = pairs.size() + B + p1dst.size() + p2dst.size() + p1src.size() + p2src.size() + 8;
     PS_CUDA(ws->child_list.ensure(sizeof(int32_t) * std::max<size_t>(1, sched_ints)));
     PS_CUDA(ws->pin_q.ensure(sizeof(int32_t) * std::max<size_t>(1, sched_ints)));
     int32_t *h_sched = ws->pin_q.as<int32_t>();
@@ -579,7 +586,9 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         o += v.size();
         return at;
     };
-    const size_t o_pairs = put(pairs), o_gdst = put(gdst), o_goff = put(goff), o_srcs = put(srcs), o_rho = put(rho);
+    const size_t o_pairs = put(pairs), o_rho = put(rho), o_p1dst = put(p1dst), o_p2dst = put(p2dst);
+    o = (o + 3) / 4 * 4;
+    const size_t o_p1src = put(p1src), o_p2src = put(p2src);
     int32_t *d_sched = ws->child_list.as<int32_t>();
     PS_CUDA(cudaMemcpyAsync(d_sched, h_sched, sizeof(int32_t) * o, cudaMemcpyHostToDevice, st));
     launch_set_slots(t, d_sched + o_pairs, (int32_t)(pairs.size() / 2), st);
@@ -616,9 +625,12 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         }
         if (S > 0) {
             ph.begin(2);  // D of this depth's dense nodes, in place in B (the MD of depth d+1)
-            if (gcount[d] > 0)
-                launch_accumulate(n, Bm, Lb, dw[d], d_sched + o_gdst + goff_at[d], d_sched + o_goff + goff_at[d],
-                                  d_sched + o_srcs, gcount[d], st);
+            const int32_t np1 = p1_at[d + 1] - p1_at[d], np2 = p2_at[d + 1] - p2_at[d];
+            if (np1 > 0)
+                launch_accumulate(n, Bm, Lb, dw[d], d_sched + o_p1dst + p1_at[d],
+                                  reinterpret_cast<const int4 *>(d_sched + o_p1src) + p1_at[d], np1,
+                                  d_sched + o_p2dst + p2_at[d],
+                                  reinterpret_cast<const int4 *>(d_sched + o_p2src) + p2_at[d], np2, st);
             ph.end();
             ++launches;
             if (d + 2 <= Dmax) {
