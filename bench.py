@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-rate", type=float, default=12.0, help="Poisson arrival rate of the serving leg (q/s)")
+    ap.add_argument("--serve-rates", default="12,60", help="Poisson arrival rates of the serving leg (q/s), comma-separated")
+    ap.add_argument("--serve-updates", type=int, default=10000, help="edges per update batch, one batch per 100 ms")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the serving leg")
     return ap.parse_args()
 
@@ -155,30 +156,45 @@ def cpu_baseline(n, s, d, qs, budget_s):
                       "queries/s extrapolated from the time per walk" % (k - 1, nr, WORKLOAD, el)}
 
 
-def serving_leg(probesim, G, qs, rate, seconds, rank):
-    """Queries arrive as a Poisson process at `rate` q/s for `seconds`; returns latency and throughput."""
+def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, rank):
+    """For each arrival rate: queries arrive as a Poisson process for `seconds` into a fresh continuous-batching
+    server (top-k, k uniform over {10, 50, 100}), while every 100 ms an update batch of updates_per_tick edges
+    (half random inserts, half deletes of edges of the original graph) enters the same FIFO.  Returns one
+    record per rate: throughput, p50/p99 latency, mean batch size, updates applied."""
     import numpy as np
-    S = probesim.Server(G, workers=2, max_batch=8, kmax=100)
     rng = np.random.default_rng(4 + rank)
-    gaps = rng.exponential(1.0 / rate, size=int(rate * seconds * 3) + 10)
-    arrivals = np.cumsum(gaps)
-    arrivals = arrivals[arrivals < seconds]
-    ks = np.array([10, 50, 100])[rng.integers(0, 3, arrivals.size)]
-    t0 = time.perf_counter()
-    done = 0
-    for i, ta in enumerate(arrivals):
-        now = time.perf_counter() - t0
-        if ta > now:
-            time.sleep(ta - now)
-        S.submit(probesim.make_queries([qs[i % len(qs)]], eps=EPS, k=int(ks[i]), query_ids=[900000 + i]))
-        done += len(S.poll(64, wait_ms=0))
-    while done < arrivals.size:
-        done += len(S.poll(64, wait_ms=500))
-    st = S.stats()
-    S.close()
-    return {"arrival_rate_qps": rate, "queries": int(arrivals.size), "qps": st["qps"], "p50_ms": st["p50_ms"],
-            "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"], "workers": 2, "max_batch": 8,
-            "k": "uniform {10, 50, 100}", "eps": EPS}
+    out = []
+    for rate in rates:
+        S = probesim.Server(G, workers=2, max_batch=8, kmax=100)
+        gaps = rng.exponential(1.0 / rate, size=int(rate * seconds * 3) + 10)
+        arrivals = np.cumsum(gaps)
+        arrivals = arrivals[arrivals < seconds]
+        ks = np.array([10, 50, 100])[rng.integers(0, 3, arrivals.size)]
+        ticks = np.arange(0.0, seconds, 0.1) if updates_per_tick > 0 else np.zeros(0)
+        events = sorted([(t, 0, i) for i, t in enumerate(arrivals)] + [(t, 1, j) for j, t in enumerate(ticks)])
+        half = updates_per_tick // 2
+        t0 = time.perf_counter()
+        done = 0
+        for ta, kind, i in events:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            if kind == 0:
+                S.submit(probesim.make_queries([qs[i % len(qs)]], eps=EPS, k=int(ks[i]), query_ids=[900000 + i]))
+            else:
+                S.update(rng.integers(0, n, half), rng.integers(0, n, half), insert=True)
+                pick = rng.integers(0, src.size, half)
+                S.update(src[pick], dst[pick], insert=False)
+            done += len(S.poll(64, wait_ms=0))
+        while done < arrivals.size:
+            done += len(S.poll(64, wait_ms=500))
+        st = S.stats()
+        S.close()
+        out.append({"arrival_rate_qps": rate, "queries": int(arrivals.size), "qps": st["qps"], "p50_ms": st["p50_ms"],
+                    "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"], "update_batches": st["updates_applied"],
+                    "edges_per_update_tick": updates_per_tick, "workers": 2, "max_batch": 8,
+                    "k": "uniform {10, 50, 100}", "eps": EPS})
+    return out
 
 
 def run_reference(args):
@@ -337,9 +353,6 @@ def run_ours(args):
                   "candidates_per_query": rsum["edge_gathers"] / rq, "levels_per_query": rsum["levels"] / rq,
                   "walk_nodes_per_query": rsum["walk_nodes"] / rq}
 
-    # serving leg: Poisson arrivals into the continuous-batching server (top-k, k in {10, 50, 100})
-    serving = serving_leg(probesim, G, qs, args.serve_rate, args.serve_seconds, rank)
-
     # end-to-end through the C ABI with host buffers: query struct in, pinned host scores out
     host_out = torch.empty((1, n), dtype=torch.float32, pin_memory=True)
     e2e_steps = min(args.steps, 30)
@@ -352,6 +365,11 @@ def run_ours(args):
     barrier()
     e2e_s = time.perf_counter() - e0
     e2e_qps = e2e_steps / e2e_s
+
+    # serving leg (last: its update batches change the graph): Poisson arrivals into the continuous-batching
+    # server at each rate, with edge-update batches every 100 ms
+    rates = [float(r) for r in args.serve_rates.split(",") if r]
+    serving = serving_leg(probesim, G, n, s, d, qs, rates, args.serve_seconds, args.serve_updates, rank)
 
     if rank != 0:
         if world > 1:

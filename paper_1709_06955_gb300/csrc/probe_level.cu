@@ -353,9 +353,11 @@ __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f,
 __device__ __forceinline__ void vatomic(float *p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void vatomic(float *p, float2 v) { atomicAdd(reinterpret_cast<float2 *>(p), v); }
 __device__ __forceinline__ void vatomic(float *p, float4 v) { atomicAdd(reinterpret_cast<float4 *>(p), v); }
-__device__ __forceinline__ void vstore(float *p, float v) { *p = v; }
-__device__ __forceinline__ void vstore(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
-__device__ __forceinline__ void vstore(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+// MD is next read a depth later by the accumulate's streaming pass: store it evict-first, so the L2 keeps the
+// gathered D tile and the in-lists
+__device__ __forceinline__ void vstore(float *p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void vstore(float *p, float2 v) { __stcs(reinterpret_cast<float2 *>(p), v); }
+__device__ __forceinline__ void vstore(float *p, float4 v) { __stcs(reinterpret_cast<float4 *>(p), v); }
 
 // NCH row gathers of one chunk: in-neighbour j's index sits in lane j % L of the group, slot j / L; past the end
 // of the piece the index is n, the zero spare row
