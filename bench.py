@@ -71,7 +71,7 @@ def recorded_traffic():
     """DRAM bytes / algorithmic bytes of the PROBE level kernel from the committed ncu summary, valid only
     while the kernel source is unchanged since the capture (checked by its hash)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1709_06955_gb300", "csrc", "probe_level.cu")
+    src = os.path.join(ROOT, "paper_1709_06955_gb300", "csrc", "pull.cu")
     summ = os.path.join(ROOT, "profiles", "k_pull_traffic.txt")
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]

@@ -147,6 +147,17 @@ inline ColLayout make_layout(int32_t n, int32_t cols) {
     return L;
 }
 
+// grid size for `work` threads in blocks of `threads`, capped at per_sm blocks per SM of the current device
+inline int grid_for(int64_t work, int threads, int per_sm) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Launchers (each launches one kernel on `s`).
 // ---------------------------------------------------------------------------------------------

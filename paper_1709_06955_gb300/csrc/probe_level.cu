@@ -28,16 +28,6 @@
 
 namespace ps {
 
-static int grid_for(int64_t work, int threads, int per_sm) {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (work + threads - 1) / threads;
-    const int64_t cap = (int64_t)sms * per_sm;
-    if (blocks > cap) blocks = cap;
-    return (int)(blocks < 1 ? 1 : blocks);
-}
-
 // zero columns [c0, c0 + w4 * 4) of every row (c0 a multiple of 4), one float4 per thread; consecutive
 // threads take consecutive float4s of a row
 __global__ void k_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t w4) {
@@ -191,7 +181,7 @@ __global__ void __launch_bounds__(kAccThreads) k_accumulate(int32_t n, float *B,
         // first parts: (part, row set) items; with fewer parts than threads, rsplit threads share a part's rows
         const int32_t rsplit = max(1, min(nr, (int32_t)blockDim.x / max(1, np1)));
         for (int32_t it = threadIdx.x; it < np1 * rsplit; it += blockDim.x) {
-            const int32_t pi = it % np1, part = it / np1;
+            const int32_t pi = rsplit == 1 ? it : it % np1, part = rsplit == 1 ? 0 : it / np1;
             const int32_t dd = __ldg(p1dst + pi);
             const int4 sc = __ldg(p1src + pi);
             const int32_t cd = S.cbase(dd & 0x3fffffff);
@@ -268,7 +258,8 @@ void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const i
                                                                              p2src, np2);
         return;
     }
-    // rows per stage: about 32 KB of rows (at least 4); two stages per block
+    // rows per stage: about 32 KB of rows (at least 4); two stages per block (48 KB stages measured slower:
+    // fewer blocks per SM)
     const int32_t R = std::max<int32_t>(1, std::min<int32_t>(256, 8192 / std::max(1, pitch)));
     const size_t smem = 2 * sizeof(float) * (size_t)R * pitch;
     const int32_t wstore = std::min(pitch, (wdense + 3) / 4 * 4);
@@ -307,177 +298,7 @@ void launch_zero_split_rows(const DeviceGraph &g, float *MD, ColLayout L, int32_
 }
 
 // ------------------------------------------------------------------------------------------------
-// pull: MD[v][tile] = w[v] * sum_{x in I(v)} D[x][tile] over one tile of T columns (grid.y = tile).
-// A group of L = T/4 lanes (1 lane for T <= 2) owns one piece of an in-list and gathers VEC = min(T,4)
-// floats per lane per in-neighbour row; pieces are ordered longest first so the groups of a warp run
-// similar trip counts.  Column indices are loaded eight at a time and broadcast within the group, so
-// eight row gathers are in flight per lane.
-// ------------------------------------------------------------------------------------------------
-template <int VEC>
-struct VecT;
-template <>
-struct VecT<1> {
-    using type = float;
-    __device__ static float load(const float *p) { return __ldg(p); }
-};
-template <>
-struct VecT<2> {
-    using type = float2;
-    __device__ static float2 load(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
-};
-template <>
-struct VecT<4> {
-    using type = float4;
-    __device__ static float4 load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-};
-
-// packed FP32x2 adds (one instruction for two lanes of a vector; each element rounds as a scalar add would)
-__device__ __forceinline__ void vadd(float &a, float b) { a += b; }
-__device__ __forceinline__ void vadd(float2 &a, float2 b) { a = __fadd2_rn(a, b); }
-__device__ __forceinline__ void vadd(float4 &a, float4 b) {
-    const float2 lo = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
-    const float2 hi = __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w));
-    a = make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-__device__ __forceinline__ float vscale(float a, float s) { return a * s; }
-__device__ __forceinline__ float2 vscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-__device__ __forceinline__ float4 vscale(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
-template <class V>
-__device__ __forceinline__ V vzero();
-template <>
-__device__ __forceinline__ float vzero<float>() { return 0.f; }
-template <>
-__device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
-template <>
-__device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-__device__ __forceinline__ void vatomic(float *p, float v) { atomicAdd(p, v); }
-__device__ __forceinline__ void vatomic(float *p, float2 v) { atomicAdd(reinterpret_cast<float2 *>(p), v); }
-__device__ __forceinline__ void vatomic(float *p, float4 v) { atomicAdd(reinterpret_cast<float4 *>(p), v); }
-// MD is next read a depth later by the accumulate's streaming pass: store it evict-first, so the L2 keeps the
-// gathered D tile and the in-lists
-__device__ __forceinline__ void vstore(float *p, float v) { __stcs(p, v); }
-__device__ __forceinline__ void vstore(float *p, float2 v) { __stcs(reinterpret_cast<float2 *>(p), v); }
-__device__ __forceinline__ void vstore(float *p, float4 v) { __stcs(reinterpret_cast<float4 *>(p), v); }
-
-// NCH row gathers of one chunk: in-neighbour j's index sits in lane j % L of the group, slot j / L; past the end
-// of the piece the index is n, the zero spare row
-template <int NCH, int L, int PER, class V, int VEC>
-__device__ __forceinline__ void pull_gather(const int32_t (&mine)[PER], unsigned gmask, const float *__restrict__ D,
-                                            int32_t dpitch, int64_t dcol0, V (&val)[NCH]) {
-#pragma unroll
-    for (int j = 0; j < NCH; ++j) {
-        const int32_t x = L == 1 ? mine[j] : __shfl_sync(gmask, mine[j / L], j % L, L);
-        val[j] = VecT<VEC>::load(D + (int64_t)x * dpitch + dcol0);
-    }
-}
-
-template <int T>
-__global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const int32_t *__restrict__ piece_v, const int64_t *__restrict__ piece_beg,
-                                              const int32_t *__restrict__ piece_len, int64_t n_pieces,
-                                              const int32_t *__restrict__ in_col, const float *__restrict__ w,
-                                              const float *__restrict__ D, int32_t dpitch, float *__restrict__ MD,
-                                              int32_t pitch, int64_t dts, int32_t dsub, int64_t mts, int32_t msub,
-                                              int32_t zrow) {
-    constexpr int VEC = T >= 4 ? 4 : T;
-    constexpr int L = T / VEC;         // lanes per group
-    constexpr int CH = 8;              // in-neighbours per chunk
-    constexpr int PER = CH / L;        // column indices loaded per lane per chunk
-    using V = typename VecT<VEC>::type;
-    const int lane = threadIdx.x & 31;
-    const int lig = lane % L;
-    const unsigned gmask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << (lane - lig));
-    const int64_t dcol0 = (int64_t)(blockIdx.y / dsub) * dts + (blockIdx.y % dsub) * T + lig * VEC;
-    const int64_t mcol0 = (int64_t)(blockIdx.y / msub) * mts + (blockIdx.y % msub) * T + lig * VEC;
-    const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / L;
-    // Software pipeline over this group's pieces p, p + ngroups, ...: the metadata of the piece after next and
-    // the column indices of the next chunk (or of the next piece's first chunk) are loaded while the current
-    // chunk's row gathers are in flight, so a short piece costs about one gather round trip.
-    auto load_meta = [&](int64_t q, int32_t &v, int64_t &beg, int32_t &info) {
-        if (q < n_pieces) {
-            v = __ldg(piece_v + q);
-            beg = __ldg(piece_beg + q);
-            info = __ldg(piece_len + q);
-        } else {
-            v = 0, beg = 0, info = 0;
-        }
-    };
-    auto load_idx = [&](int64_t beg, int32_t len, int32_t e0, int32_t(&mine)[PER]) {
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int32_t e = e0 + lig + L * r;
-            mine[r] = e < len ? __ldg(in_col + beg + e) : zrow;
-        }
-    };
-    int64_t p = gid;
-    int32_t v, info, v1, info1;
-    int64_t beg, beg1;
-    load_meta(p, v, beg, info);
-    load_meta(p + ngroups, v1, beg1, info1);
-    int32_t mine[PER];
-    load_idx(beg, info & 0x7fffffff, 0, mine);
-    for (; p < n_pieces; p += ngroups) {
-        int32_t v2, info2;
-        int64_t beg2;
-        load_meta(p + 2 * ngroups, v2, beg2, info2);
-        const float wv = __ldg(w + v);
-        const int32_t len = info & 0x7fffffff;
-        V acc = vzero<V>();
-        if (len == 0) {  // an empty in-list (about half the rows of a power-law graph): the row is zero
-            load_idx(beg1, info1 & 0x7fffffff, 0, mine);
-        } else {
-            for (int32_t e0 = 0;;) {
-                V val[CH];
-                pull_gather<CH, L, PER, V, VEC>(mine, gmask, D, dpitch, dcol0, val);
-                e0 += CH;
-                const bool more = e0 < len;
-                if (more) load_idx(beg, len, e0, mine);
-                else load_idx(beg1, info1 & 0x7fffffff, 0, mine);
-#pragma unroll
-                for (int j = 0; j < CH; ++j) vadd(acc, val[j]);
-                if (!more) break;
-            }
-        }
-        const V res = vscale(acc, wv);
-        float *dst = MD + (int64_t)v * pitch + mcol0;
-        if (info < 0) vatomic(dst, res); else vstore(dst, res);
-        v = v1, beg = beg1, info = info1;
-        v1 = v2, beg1 = beg2, info1 = info2;
-    }
-}
-
-int32_t pull_tile_for(int32_t S, int32_t wide) {
-    if (S <= 1) return 1;
-    if (S <= 2) return 2;
-    if (S <= 4) return 4;
-    if (S <= 8) return 8;
-    if (S <= 16 || wide <= 16) return 16;
-    return 32;
-}
-
-void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t dts, int32_t dsub, float *MD,
-                 int32_t pitch, int64_t mts, int32_t msub, int32_t ntiles, int32_t tile, int32_t blocks_per_sm,
-                 cudaStream_t s) {
-    if (ntiles <= 0) return;
-    const int L = tile >= 4 ? tile / 4 : 1;
-    const int64_t threads_needed = g.n_pieces * L;
-    const int blocks = grid_for(threads_needed, 256, blocks_per_sm > 0 ? blocks_per_sm : 8);
-    dim3 grid(blocks, ntiles);
-#define PS_PULL(T) k_pull<T><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, \
-                                                  dpitch, MD, pitch, dts, dsub, mts, msub, g.n)
-    switch (tile) {
-        case 1: PS_PULL(1); break;
-        case 2: PS_PULL(2); break;
-        case 4: PS_PULL(4); break;
-        case 8: PS_PULL(8); break;
-        case 16: PS_PULL(16); break;
-        default: PS_PULL(32); break;
-    }
-#undef PS_PULL
-}
-
-// ------------------------------------------------------------------------------------------------
-// gamma: one warp per tree node t at the current depth.
+// gamma, for every tree node t at the current depth:
 //   beta_t  = sqrt(c)/|I(a_t)| * (sum_{x in I(a_t)} MD(t)[x] + G_t)   (the score PROBE would give a_t)
 //   gamma_t = w_t / n_r - beta_t;  G_parent += gamma_t
 // ------------------------------------------------------------------------------------------------
