@@ -381,7 +381,7 @@ def run_ours(args):
     achieved = prof["probe_bytes"] / (prof["probe_ms"] / 1e3) / 1e9 if prof["probe_ms"] > 0 else None
     ratio = recorded_traffic()
     per_launch = prof["probe_bytes"] / max(1, prof["probe_launches"])
-    roof = {"kernel": "k_pull (PROBE level pull, probe_level.cu)", "bound": "hbm", "achieved": achieved,
+    roof = {"kernel": "k_pull (PROBE level pull, pull.cu)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_kind": peak_kind + " hbm_gbs (copy)", "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": (ratio * per_launch) if ratio else None,
