@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--serve-rates", default="12,60", help="Poisson arrival rates of the serving leg (q/s), comma-separated")
     ap.add_argument("--serve-updates", type=int, default=10000, help="edges per update batch, one batch per 100 ms")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the serving leg")
+    ap.add_argument("--mixed-batch", type=int, default=0,
+                    help="queries of the optional mixed-eps top-k leg (eps 0.1 / 0.05 alternating, k = 50); 0 = off")
     return ap.parse_args()
 
 
@@ -127,6 +129,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def describe_workload(name, n, m):
+    """The workload's text for the JSON line, from its name and actual sizes."""
+    import math
+    kind = "R-MAT (.57,.19,.19,.05)" if name.startswith("rmat") else "Chung-Lu (exponent 2.1)"
+    return "%s n=2^%d m=%d seed 1, eps=%g delta=0.01 c=0.6" % (kind, int(round(math.log2(n))), m, EPS)
+
+
 def load_workload(name):
     from paper_1709_06955_gb300 import synth
     n, s, d = synth.config_graph(name)
@@ -153,7 +162,7 @@ def cpu_baseline(n, s, d, qs, budget_s):
     per_walk = el / k
     return {"value": 1.0 / (per_walk * nr), "unit": "queries/s", "cores": 1, "kind": "oracle",
             "sample": "walks 0..%d of 1 query (of n_r=%d) on %s, Alg. 1 FP64 single-threaded, %.1f s; "
-                      "queries/s extrapolated from the time per walk" % (k - 1, nr, WORKLOAD, el)}
+                      "queries/s extrapolated from the time per walk" % (k - 1, nr, "%d-node graph" % n, el)}
 
 
 def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, rank):
@@ -218,7 +227,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "R-MAT (.57,.19,.19,.05) n=2^20 m=2^24, eps=0.1 delta=0.01 c=0.6",
+            "config": {"workload": describe_workload(args.workload, n, len(s)),
                        "step": "one walk of one query (Alg. 1 on it), queries/s = walks/s / n_r"},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
                              "sample": "%d walks over %d queries (of n_r=%d each)" % (args.steps, min(args.steps, len(qs)), nr)},
@@ -333,6 +342,28 @@ def run_ours(args):
     # the batches hold the first nb * B queries of the timed leg: the same queries one at a time
     single_same_qps = nb * B / (sum(lat[:nb * B]) / 1e3)
 
+    # optional mixed-eps top-k leg (the batched configuration's pattern): one call of --mixed-batch queries,
+    # eps alternating 0.1 / 0.05 (uneven n_r), top-50 per query; the library cuts the call into batches that
+    # fit its workspace budget
+    mixed = None
+    if args.mixed_batch > 0:
+        MB = args.mixed_batch
+        eps_mix = [EPS if j % 2 == 0 else EPS / 2 for j in range(MB)]
+        Qm = probesim.make_queries([qs[(rank * 100003 + 5000 + j) % nq] for j in range(MB)], eps=eps_mix, k=50,
+                                   query_ids=[rank * 100003 + 5000 + j for j in range(MB)])
+        mids = torch.empty((MB, 50), dtype=torch.int32, device=dev)
+        mvals = torch.empty((MB, 50), dtype=torch.float32, device=dev)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.topk(Qm, kmax=50, ids=mids, vals=mvals, stream=sptr)
+        b.record(stream)
+        barrier()
+        mms = a.elapsed_time(b)
+        mixed = {"queries": MB, "eps": "%g / %g alternating" % (EPS, EPS / 2), "k": 50, "value": MB / (mms / 1e3),
+                 "unit": "queries/s", "ms": mms,
+                 "n_r": [int(G.num_walks(EPS)), int(G.num_walks(EPS / 2))]}
+
     # randomized PROBE (Alg. 3) on the same graph: a few queries one at a time
     GR = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_RANDOMIZED)
     rq = 10
@@ -397,8 +428,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "R-MAT (.57,.19,.19,.05) n=2^20 m=2^24 seed 1, eps=0.1 delta=0.01 c=0.6 "
-                                   "(n_r=3325), deterministic PROBE, one query per call",
+            "config": {"workload": describe_workload(args.workload, n, len(s)) +
+                                   " (n_r=%d), deterministic PROBE, one query per call" % G.num_walks(EPS),
                        "queries": "uniform over nodes with in-degree >= 1", "l2": "flushed between steps (256 MB write)",
                        "pull_tuning": tuning,
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -411,6 +442,7 @@ def run_ours(args):
             "phases_ms_per_query": {k: v / np_ for k, v in phases.items()},
             "profiled_ms_per_query": prof["step_ms"] / np_,
             "randomized_probe": randomized,
+            "mixed_eps_topk": mixed,
             "serving": serving,
             "work": {"walks_per_query": agg["walks"] / args.steps, "tree_nodes_per_query": agg["tree_nodes"] / args.steps,
                      "vectors_per_query": agg["vectors"] / args.steps,
