@@ -62,8 +62,8 @@ struct PinnedBuf {
 struct Workspace {
     DevBuf qbuf, walks, lens, ctr;
     DevBuf t_key, t_node, t_parent, t_depth, t_query, t_weight, t_height, t_slot, t_gamma, t_G;
-    DevBuf counts, offs, node_list, slot_entry, nchild, child_off, child_list, ccur, rho_slot;
-    DevBuf md_a, md_b, dmat, out_stage;
+    DevBuf counts, offs, node_list, col_export, sched;  // level schedule: exported column nodes, uploaded plan
+    DevBuf md_a, md_b, out_stage;                       // the two score buffers; host-output staging
     DevBuf r_cnt, r_off, r_part, r_iwalk, r_ilen, r_iq, r_ik, r_fi[2], r_fn[2], r_keys[2], r_deg, r_pref, r_counts, r_ctr;
     DevBuf tk_hist, tk_state, tk_tie, tk_cid, tk_cval, tk_ids, tk_vals, tk_qk;
     PinnedBuf pin_q;  // query arrays of one batch
@@ -85,8 +85,8 @@ struct Workspace {
     }
     void release() {
         DevBuf *bufs[] = {&qbuf, &walks, &lens, &ctr, &t_key, &t_node, &t_parent, &t_depth, &t_query, &t_weight,
-                          &t_height, &t_slot, &t_gamma, &t_G, &counts, &offs, &node_list, &slot_entry, &nchild,
-                          &child_off, &child_list, &ccur, &rho_slot, &md_a, &md_b, &dmat, &out_stage, &r_cnt, &r_off,
+                          &t_height, &t_slot, &t_gamma, &t_G, &counts, &offs, &node_list, &col_export,
+                          &sched, &md_a, &md_b, &out_stage, &r_cnt, &r_off,
                           &r_part, &r_iwalk, &r_ilen, &r_iq, &r_ik, &r_fi[0], &r_fi[1], &r_fn[0], &r_fn[1],
                           &r_keys[0], &r_keys[1], &r_deg, &r_pref, &r_counts, &r_ctr, &tk_hist, &tk_state, &tk_tie,
                           &tk_cid, &tk_cval, &tk_ids, &tk_vals, &tk_qk};

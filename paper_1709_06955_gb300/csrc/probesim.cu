@@ -421,8 +421,8 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     // the parent and nothing is copied.  Push columns (height 2) sit in a block after the dense columns.
     int32_t ncol_nodes = 0;
     for (int32_t d = 0; d < D1; ++d) ncol_nodes += scount[d] + hcount[d];
-    PS_CUDA(ws->slot_entry.ensure(sizeof(int32_t) * (5 * (size_t)std::max(1, ncol_nodes) + 1)));
-    int32_t *d_exp = ws->slot_entry.as<int32_t>(), *d_expn = d_exp + 5 * (size_t)std::max(1, ncol_nodes);
+    PS_CUDA(ws->col_export.ensure(sizeof(int32_t) * (5 * (size_t)std::max(1, ncol_nodes) + 1)));
+    int32_t *d_exp = ws->col_export.as<int32_t>(), *d_expn = d_exp + 5 * (size_t)std::max(1, ncol_nodes);
     PS_CUDA(cudaMemsetAsync(d_expn, 0, sizeof(int32_t), st));
     launch_sched_export(t, d_exp, d_expn, st);
     ph.end();
@@ -485,13 +485,10 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         for (int32_t x = ch.head; x >= 0; x = heir[x]) col[x] = c;
     }
     std::vector<int32_t> width(D1, 0), rho(B, -1);
-    int32_t maxw = 0, maxh = 0;
     for (int32_t d = 0; d <= Dmax; ++d) {
         int32_t w = 0;
         for (int32_t i : dense_at[d]) w = std::max(w, col[i] + 1);
         width[d] = w;
-        maxw = std::max(maxw, w);
-        maxh = std::max(maxh, (int32_t)push_at[d].size());
         if (d == 0)
             for (int32_t i : dense_at[0]) rho[h_exp[5 * i + 4]] = col[i];
     }
@@ -576,7 +573,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     p2_at[D1] = (int32_t)p2dst.size();
     // upload: slot pairs, super-root columns, part destinations, part sources (int4, 16-byte aligned)
     const size_t sched_ints = pairs.size() + B + p1dst.size() + p2dst.size() + p1src.size() + p2src.size() + 8;
-    PS_CUDA(ws->child_list.ensure(sizeof(int32_t) * std::max<size_t>(1, sched_ints)));
+    PS_CUDA(ws->sched.ensure(sizeof(int32_t) * std::max<size_t>(1, sched_ints)));
     PS_CUDA(ws->pin_q.ensure(sizeof(int32_t) * std::max<size_t>(1, sched_ints)));
     int32_t *h_sched = ws->pin_q.as<int32_t>();
     size_t o = 0;
@@ -589,7 +586,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     const size_t o_pairs = put(pairs), o_rho = put(rho), o_p1dst = put(p1dst), o_p2dst = put(p2dst);
     o = (o + 3) / 4 * 4;
     const size_t o_p1src = put(p1src), o_p2src = put(p2src);
-    int32_t *d_sched = ws->child_list.as<int32_t>();
+    int32_t *d_sched = ws->sched.as<int32_t>();
     PS_CUDA(cudaMemcpyAsync(d_sched, h_sched, sizeof(int32_t) * o, cudaMemcpyHostToDevice, st));
     launch_set_slots(t, d_sched + o_pairs, (int32_t)(pairs.size() / 2), st);
     ++launches;
@@ -691,7 +688,6 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         ws->stats.levels += 1;
     }
     float *MD0 = Bm;  // after the last swap, the super-roots' MD
-    (void)maxw;
     // 5. estimates: s(u, v) = MD(super-root)[v], s(u, u) = 1
     ph.begin(8);
     launch_finalize(n, B, qb.node, d_rho, scount[0] > 0 ? MD0 : nullptr, lay[0], dg.ext2int, d_out, st);
