@@ -137,7 +137,9 @@ typedef struct {
     int64_t kernel_launches;/* all kernels this library launched in the call */
     double phase_ms[12];    /* profiling on: CUDA-event time per phase of the deterministic path: 0 walks,
                                1 walk tree and level schedule, 2 D accumulate, 3 gamma scatter, 4 split-row
-                               zeroing, 5 pull, 6 push columns, 7 gamma, 8 estimates; 9-11 unused */
+                               zeroing, 5 pull, 6 push columns, 7 gamma, 8 estimates.  9 (always recorded):
+                               host wall-clock time of the column schedule, during which the device waits;
+                               10-11 unused */
     int64_t max_columns;    /* widest score matrix of the level loop, in columns (deterministic path) */
 } probesim_stats;
 

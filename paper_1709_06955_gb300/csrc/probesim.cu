@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -431,22 +432,36 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     int32_t *h_exp = ws->pin_q.as<int32_t>();
     PS_CUDA(cudaMemcpyAsync(h_exp, d_exp, sizeof(int32_t) * 5 * (size_t)ncol_nodes, cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
+    const auto host0 = std::chrono::steady_clock::now();  // the host-side schedule starts (the device waits)
     // export rows: 0 entry, 1 depth, 2 parent entry, 3 dense, 4 query
-    std::unordered_map<int32_t, int32_t> row_of;
-    row_of.reserve(2 * (size_t)ncol_nodes + 1);
     std::vector<std::vector<int32_t>> dense_at(D1), push_at(D1);
-    for (int32_t i = 0; i < ncol_nodes; ++i) {
-        row_of[h_exp[5 * i]] = i;
-        (h_exp[5 * i + 3] ? dense_at : push_at)[h_exp[5 * i + 1]].push_back(i);
+    for (int32_t i = 0; i < ncol_nodes; ++i) (h_exp[5 * i + 3] ? dense_at : push_at)[h_exp[5 * i + 1]].push_back(i);
+    // the export row of every node's parent (-1: none).  Tree entries are slots of the table, so a flat array
+    // indexes them unless the table is much larger than the exported set
+    std::vector<int32_t> prow(ncol_nodes, -1);
+    if (t.cap <= 32 * (int64_t)ncol_nodes + 65536) {
+        std::vector<int32_t> row_of((size_t)t.cap, -1);
+        for (int32_t i = 0; i < ncol_nodes; ++i) row_of[h_exp[5 * i]] = i;
+        for (int32_t i = 0; i < ncol_nodes; ++i) {
+            const int32_t pe = h_exp[5 * i + 2];
+            if (pe >= 0) prow[i] = row_of[pe];
+        }
+    } else {
+        std::unordered_map<int32_t, int32_t> row_of;
+        row_of.reserve(2 * (size_t)ncol_nodes + 1);
+        for (int32_t i = 0; i < ncol_nodes; ++i) row_of[h_exp[5 * i]] = i;
+        for (int32_t i = 0; i < ncol_nodes; ++i) {
+            const auto it = row_of.find(h_exp[5 * i + 2]);
+            if (it != row_of.end()) prow[i] = it->second;
+        }
     }
     // heights are not exported; the heir is the dense child with the deepest dense descendant chain, found
     // bottom-up, ties to the smaller entry
     std::vector<int32_t> chain(ncol_nodes, 0), heir(ncol_nodes, -1), col(ncol_nodes, -1);
     for (int32_t d = Dmax; d >= 1; --d)
         for (int32_t i : dense_at[d]) {
-            const auto it = row_of.find(h_exp[5 * i + 2]);
-            if (it == row_of.end()) continue;
-            const int32_t pr = it->second;
+            const int32_t pr = prow[i];
+            if (pr < 0) continue;
             const int32_t h = heir[pr];
             if (h < 0 || chain[i] > chain[h] || (chain[i] == chain[h] && h_exp[5 * i] < h_exp[5 * h])) heir[pr] = i;
             chain[pr] = std::max(chain[pr], chain[i] + 1);
@@ -519,10 +534,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     // adjacent for the accumulate
     for (int32_t d = 0; d <= Dmax; ++d) {
         std::vector<int32_t> &pa = push_at[d];
-        auto pcol = [&](int32_t x) {
-            const auto it = d >= 1 ? row_of.find(h_exp[5 * x + 2]) : row_of.end();
-            return it == row_of.end() ? -1 : col[it->second];
-        };
+        auto pcol = [&](int32_t x) { return d >= 1 && prow[x] >= 0 ? col[prow[x]] : -1; };
         std::sort(pa.begin(), pa.end(), [&](int32_t x, int32_t y) {
             const int32_t px = pcol(x), py = pcol(y);
             return px != py ? px < py : h_exp[5 * x] < h_exp[5 * y];
@@ -538,8 +550,8 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     // srcs = columns (at d+1) of its children other than the heir
     std::vector<std::vector<int32_t>> kids(ncol_nodes);
     for (int32_t i = 0; i < ncol_nodes; ++i) {
-        const auto it = row_of.find(h_exp[5 * i + 2]);
-        if (it != row_of.end() && heir[it->second] != i) kids[it->second].push_back(col[i]);
+        const int32_t pr = prow[i];
+        if (pr >= 0 && heir[pr] != i) kids[pr].push_back(col[i]);
     }
     // Each group is cut into parts of at most four sources, stored as a destination (bit 30: set, for a node
     // without heir) and an int4 of sources (-1 = none).  The first part of every group runs in the
@@ -588,6 +600,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     const size_t o_p1src = put(p1src), o_p2src = put(p2src);
     int32_t *d_sched = ws->sched.as<int32_t>();
     PS_CUDA(cudaMemcpyAsync(d_sched, h_sched, sizeof(int32_t) * o, cudaMemcpyHostToDevice, st));
+    ws->stats.phase_ms[9] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - host0).count();
     launch_set_slots(t, d_sched + o_pairs, (int32_t)(pairs.size() / 2), st);
     ++launches;
     const int32_t *d_rho = d_sched + o_rho;

@@ -41,7 +41,8 @@ class Stats(C.Structure):
                 ("probe_ms", C.c_double), ("probe_bytes", C.c_double), ("kernel_launches", C.c_int64),
                 ("phase_ms", C.c_double * 12), ("max_columns", C.c_int64)]
 
-    PHASES = ["walks", "tree", "accumulate", "scatter", "zero_rows", "pull", "push", "gamma", "estimates"]
+    PHASES = ["walks", "tree", "accumulate", "scatter", "zero_rows", "pull", "push", "gamma", "estimates",
+              "host_schedule"]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
