@@ -169,10 +169,11 @@ void launch_sched_count(TrieTable t, int32_t *ncount, int32_t *scount, int32_t *
 void launch_sched_export(TrieTable t, int32_t *out, int32_t *count, cudaStream_t s);
 void launch_node_lists(TrieTable t, const int32_t *node_off, int32_t *ncur, int32_t *node_list, cudaStream_t s);
 void launch_set_slots(TrieTable t, const int32_t *pairs, int32_t count, cudaStream_t s);
-void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, ColLayout L, int32_t h0,
-                          cudaStream_t s);
+void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, ColLayout L, cudaStream_t s);
+// inherited = false: push nodes whose column is in the push block (slot >= h0); true: those whose column
+// was inherited from the parent (slot < h0)
 void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, ColLayout L,
-                    int32_t h0, cudaStream_t s);
+                    int32_t h0, bool inherited, cudaStream_t s);
 // Parts of at most four sources: p1 (the first part of every group: bit 30 of the destination = set, else add)
 // then p2 (later parts: add).  Sources are -1 where absent; the destinations are columns < wdense.
 void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *p1dst, const int4 *p1src,
@@ -186,9 +187,10 @@ void launch_zero_spare_row(float *MD, ColLayout L, int32_t width, cudaStream_t s
 // first tile's column in row 0; their rows are dpitch / pitch floats apart; tile j of D starts (j / dsub) * dts +
 // (j % dsub) * tile floats after the first, and likewise for MD with mts / msub (ColLayout::tile_stride/sub).
 // Row n of D (the spare row) must be zero over the pulled columns.
+// zmask (may be null): bit i of word k set = column 32k + i of the launch's columns is written as 0
 void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t dts, int32_t dsub, float *MD,
                  int32_t pitch, int64_t mts, int32_t msub, int32_t ntiles, int32_t tile, int32_t blocks_per_sm,
-                 cudaStream_t s);
+                 const uint32_t *zmask, cudaStream_t s);
 void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, const float *inv_nr,
                   const float *MD, ColLayout L, cudaStream_t s);
 void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,

@@ -39,50 +39,65 @@ __global__ void k_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32
     }
 }
 
-// zeroes columns [c0, c0 + width) and up to the next multiple of 4 (padding of the push block)
-void launch_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width, cudaStream_t s) {
-    if (width <= 0) return;
-    const int32_t w4 = (width + 3) / 4;
-    const int blocks = grid_for((int64_t)n * w4, 256, 8);
-    k_zero_cols<<<blocks, 256, 0, s>>>(n, MD, L, c0, w4);
+// zero columns [c0, c1) of every row, c1 - c0 < 4 (the head of a range that does not start on a float4)
+__global__ void k_zero_cols_head(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t c1) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    for (int32_t c = c0; c < c1; ++c) MD[L.at(v, c)] = 0.f;
 }
 
+// zeroes columns [c0, c0 + width) rounded up to a multiple of 4 (inside the pitch)
+void launch_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width, cudaStream_t s) {
+    if (width <= 0) return;
+    const int32_t end = (c0 + width + 3) / 4 * 4, a0 = (c0 + 3) / 4 * 4;
+    if (a0 > c0) k_zero_cols_head<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, MD, L, c0, std::min(a0, end));
+    if (end > a0) {
+        const int32_t w4 = (end - a0) / 4;
+        const int blocks = grid_for((int64_t)n * w4, 256, 8);
+        k_zero_cols<<<blocks, 256, 0, s>>>(n, MD, L, a0, w4);
+    }
+}
+
+// a tree node with a push column: subtree height 2, below the super-root
+__device__ __forceinline__ bool is_push_node(const TrieTable &t, int32_t e) { return t.height[e] == 2 && t.depth[e] != 0; }
+
 // ------------------------------------------------------------------------------------------------
-// scatter: for every tree node g at depth t+2 whose grandparent has a dense column (< h0, the first push
-// column of the grandparent's depth), D[a_g][slot(grandparent(g))] += gamma_g.
+// scatter: for every tree node g at depth t+2 whose grandparent is dense,
+// D[a_g][slot(grandparent(g))] += gamma_g.
 // ------------------------------------------------------------------------------------------------
-__global__ void k_scatter_gamma(const int32_t *__restrict__ nodes, int32_t cnt, TrieTable t, float *D, ColLayout L,
-                                int32_t h0) {
+__global__ void k_scatter_gamma(const int32_t *__restrict__ nodes, int32_t cnt, TrieTable t, float *D, ColLayout L) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cnt) return;
     const int32_t e = nodes[i];
-    const int32_t sl = t.slot[t.parent[t.parent[e]]];
-    if (sl < 0 || sl >= h0) return;
+    const int32_t gp = t.parent[t.parent[e]];
+    const int32_t sl = t.slot[gp];
+    if (sl < 0 || is_push_node(t, gp)) return;
     atomicAdd(D + L.at(t.node[e], sl), t.gamma[e]);
 }
 
-void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, ColLayout L, int32_t h0,
-                          cudaStream_t s) {
+void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float *D, ColLayout L, cudaStream_t s) {
     if (cnt <= 0) return;
-    k_scatter_gamma<<<(cnt + 255) / 256, 256, 0, s>>>(nodes, cnt, t, D, L, h0);
+    k_scatter_gamma<<<(cnt + 255) / 256, 256, 0, s>>>(nodes, cnt, t, D, L);
 }
 
 // ------------------------------------------------------------------------------------------------
-// push: for every tree node g at depth t+2 whose grandparent p has a push column (>= h0):
-// MD[x][slot(p)] += sqrt(c)/|I(x)| * gamma_g for every x in O(a_g).  One block per node g: an out-list can
-// hold tens of thousands of edges (hubs), so the block's threads split it and a hub does not hold up the
-// launch.
+// push: for every tree node g at depth t+2 whose grandparent p is a push node:
+// MD[x][slot(p)] += sqrt(c)/|I(x)| * gamma_g for every x in O(a_g).  A push node's column is either in the
+// push block of its depth (slot >= h0) or the column it inherited from its parent (slot < h0); one launch
+// serves one of the two kinds.  One block per node g: an out-list can hold tens of thousands of edges
+// (hubs), so the block's threads split it and a hub does not hold up the launch.
 // ------------------------------------------------------------------------------------------------
 constexpr int kListThreads = 128;
 
 __global__ void __launch_bounds__(kListThreads) k_push_h2(const int64_t *__restrict__ out_off,
                                                           const int32_t *__restrict__ out_col,
                                                           const float *__restrict__ w, const int32_t *__restrict__ nodes,
-                                                          TrieTable t, float *MD, ColLayout L, int32_t h0) {
+                                                          TrieTable t, float *MD, ColLayout L, int32_t h0,
+                                                          int32_t inherited) {
     const int32_t e = nodes[blockIdx.x];
     const int32_t p = t.parent[t.parent[e]];  // the height-2 node
     const int32_t sl = t.slot[p];
-    if (sl < h0) return;
+    if (sl < 0 || !is_push_node(t, p) || (sl < h0) != (inherited != 0)) return;
     const int32_t a = t.node[e];
     const float g = t.gamma[e];
     const int64_t beg = out_off[a], end = out_off[a + 1];
@@ -95,9 +110,9 @@ __global__ void __launch_bounds__(kListThreads) k_push_h2(const int64_t *__restr
 }
 
 void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, ColLayout L,
-                    int32_t h0, cudaStream_t s) {
+                    int32_t h0, bool inherited, cudaStream_t s) {
     if (cnt <= 0) return;
-    k_push_h2<<<(unsigned)cnt, kListThreads, 0, s>>>(g.out_off, g.out_col, g.w, nodes, t, MD, L, h0);
+    k_push_h2<<<(unsigned)cnt, kListThreads, 0, s>>>(g.out_off, g.out_col, g.w, nodes, t, MD, L, h0, inherited ? 1 : 0);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -253,7 +268,8 @@ void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const i
     const int32_t pitch = L.K > 0 ? L.K * kGroup : L.R;  // staged row width (a multiple of 4)
     // staging pays when a stage holds a few rows to spread each part's set-up over; wider rows (batches of
     // queries) go straight to global memory
-    if (pitch > 2048) {
+    // few parts (deep depths) touch a few sectors of each row: cheaper in place than streaming whole rows
+    if (pitch > 2048 || (int64_t)(np1 + np2) * 40 < pitch) {
         k_accumulate_direct<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(n, B, L, p1dst, p1src, np1, p2dst,
                                                                              p2src, np2);
         return;

@@ -466,7 +466,20 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
             if (h < 0 || chain[i] > chain[h] || (chain[i] == chain[h] && h_exp[5 * i] < h_exp[5 * h])) heir[pr] = i;
             chain[pr] = std::max(chain[pr], chain[i] + 1);
         }
-    // a chain is a maximal path of heirs; all its nodes share one column.  Chains are coloured deepest bottom
+    // a dense node without a dense heir takes its first push child (smallest entry) as "push heir": that
+    // child's pushed column is then the node's D column, in place, and the accumulate has nothing to copy
+    std::vector<int32_t> pheir(ncol_nodes, -1);
+    for (int32_t d = 1; d <= Dmax; ++d)
+        for (int32_t i : push_at[d]) {
+            const int32_t pr = prow[i];
+            if (pr < 0 || heir[pr] >= 0) continue;
+            if (pheir[pr] < 0 || h_exp[5 * i] < h_exp[5 * pheir[pr]]) pheir[pr] = i;
+        }
+    std::vector<char> is_pheir(ncol_nodes, 0);
+    for (int32_t i = 0; i < ncol_nodes; ++i)
+        if (pheir[i] >= 0) is_pheir[pheir[i]] = 1;
+    // a chain is a maximal path of heirs (ending, possibly, in a push heir); all its nodes share one column.
+    // Chains are coloured deepest bottom
     // first, each taking the smallest column whose chains all start more than one depth below its bottom
     // (every chain coloured before it ends at least as deep, so that is "free over its depth range and the
     // depth below"); the columns in use at a depth then stay close to the number of dense nodes there.
@@ -482,6 +495,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
             if (is_heir[i]) continue;
             int32_t x = i, bot = d;
             while (heir[x] >= 0) x = heir[x], ++bot;
+            if (pheir[x] >= 0) ++bot;
             chains.push_back({i, d, bot});
         }
     std::sort(chains.begin(), chains.end(), [&](const Chain &x, const Chain &y) {
@@ -497,7 +511,9 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         while (c < (int32_t)top_min.size() && top_min[c] <= ch.bottom + 1) ++c;
         if (c == (int32_t)top_min.size()) top_min.push_back(ch.top);
         top_min[c] = std::min(top_min[c], ch.top);
-        for (int32_t x = ch.head; x >= 0; x = heir[x]) col[x] = c;
+        int32_t last = ch.head;
+        for (int32_t x = ch.head; x >= 0; x = heir[x]) col[x] = c, last = x;
+        if (pheir[last] >= 0) col[pheir[last]] = c;
     }
     std::vector<int32_t> width(D1, 0), rho(B, -1);
     for (int32_t d = 0; d <= Dmax; ++d) {
@@ -517,8 +533,16 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         tail[d] = rem > 0 ? pull_tile_for(rem, 16) : 0;
         dw[d] = 32 * full + tail[d];
     }
+    // push nodes of a depth that keep a column of their own (the others inherited their parent's)
+    std::vector<int32_t> hinh(D1, 0);
+    for (int32_t d = 0; d <= Dmax; ++d) {
+        std::vector<int32_t> &pa = push_at[d];
+        const size_t before = pa.size();
+        pa.erase(std::remove_if(pa.begin(), pa.end(), [&](int32_t x) { return is_pheir[x] != 0; }), pa.end());
+        hinh[d] = (int32_t)(before - pa.size());
+    }
     // MD of depth d is read in place as D of depth d-1, so its matrix holds the columns of both depths:
-    // max(dw[d-1], dw[d]) dense columns, then the push block of depth d at h0[d]
+    // max(dw[d-1], dw[d]) dense columns (inherited push columns among them), then the push block at h0[d]
     std::vector<int32_t> h0v(D1, 0), rpv(D1, 0);
     std::vector<ColLayout> lay(D1);
     int64_t max_floats = 4 * (int64_t)n;
@@ -546,12 +570,12 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         *too_big = B > 1;
         return fail(PROBESIM_E_NOMEM, "score vectors of one query exceed the workspace budget");
     }
-    // accumulate groups per depth d (dense parents at d): dst = parent column (| set flag when it has no heir),
-    // srcs = columns (at d+1) of its children other than the heir
+    // accumulate groups per depth d (dense parents at d): dst = parent column (| set flag when it has no heir
+    // of either kind), srcs = columns (at d+1) of its children other than the heir
     std::vector<std::vector<int32_t>> kids(ncol_nodes);
     for (int32_t i = 0; i < ncol_nodes; ++i) {
         const int32_t pr = prow[i];
-        if (pr >= 0 && heir[pr] != i) kids[pr].push_back(col[i]);
+        if (pr >= 0 && heir[pr] != i && pheir[pr] != i) kids[pr].push_back(col[i]);
     }
     // Each group is cut into parts of at most four sources, stored as a destination (bit 30: set, for a node
     // without heir) and an int4 of sources (-1 = none).  The first part of every group runs in the
@@ -576,15 +600,33 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         std::sort(dense_at[d].begin(), dense_at[d].end(), [&](int32_t x, int32_t y) { return col[x] < col[y]; });
         for (int32_t i : dense_at[d]) {
             std::sort(kids[i].begin(), kids[i].end());
-            if (kids[i].empty() && heir[i] >= 0) continue;  // its column already is its heir's MD
-            put_part(p1dst, p1src, col[i] | (heir[i] < 0 ? (1 << 30) : 0), kids[i], 0);
+            const bool own = heir[i] < 0 && pheir[i] < 0;  // no heir of any kind: the column is set
+            if (kids[i].empty() && !own) continue;            // its column already is its heir's MD
+            put_part(p1dst, p1src, col[i] | (own ? (1 << 30) : 0), kids[i], 0);
             for (size_t f = 4; f < kids[i].size(); f += 4) put_part(p2dst, p2src, col[i], kids[i], f);
         }
     }
     p1_at[D1] = (int32_t)p1dst.size();
     p2_at[D1] = (int32_t)p2dst.size();
-    // upload: slot pairs, super-root columns, part destinations, part sources (int4, 16-byte aligned)
-    const size_t sched_ints = pairs.size() + B + p1dst.size() + p2dst.size() + p1src.size() + p2src.size() + 8;
+    // zero masks of the pull at each depth: an inherited push column inside the pulled tiles is written as 0
+    // there (the push fills it afterwards); one 32-bit word per 32 columns, words of depth d at zoff[d]
+    std::vector<int32_t> zmask, zoff(D1 + 1, 0), zany(D1, 0);
+    for (int32_t d = 0; d < D1; ++d) {
+        zoff[d] = (int32_t)zmask.size();
+        zmask.resize(zmask.size() + (size_t)(dw[d] + 31) / 32, 0);
+    }
+    zoff[D1] = (int32_t)zmask.size();
+    for (int32_t i = 0; i < ncol_nodes; ++i) {
+        if (!is_pheir[i]) continue;
+        const int32_t d = h_exp[5 * i + 1], c = col[i];
+        if (c < dw[d]) {
+            zmask[zoff[d] + c / 32] |= (int32_t)(1u << (c % 32));
+            zany[d] = 1;
+        }
+    }
+    // upload: slot pairs, super-root columns, part destinations, zero masks, part sources (int4, 16-byte aligned)
+    const size_t sched_ints =
+        pairs.size() + B + p1dst.size() + p2dst.size() + zmask.size() + p1src.size() + p2src.size() + 8;
     PS_CUDA(ws->sched.ensure(sizeof(int32_t) * std::max<size_t>(1, sched_ints)));
     PS_CUDA(ws->pin_q.ensure(sizeof(int32_t) * std::max<size_t>(1, sched_ints)));
     int32_t *h_sched = ws->pin_q.as<int32_t>();
@@ -595,7 +637,8 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         o += v.size();
         return at;
     };
-    const size_t o_pairs = put(pairs), o_rho = put(rho), o_p1dst = put(p1dst), o_p2dst = put(p2dst);
+    const size_t o_pairs = put(pairs), o_rho = put(rho), o_p1dst = put(p1dst), o_p2dst = put(p2dst),
+                 o_zmask = put(zmask);
     o = (o + 3) / 4 * 4;
     const size_t o_p1src = put(p1src), o_p2src = put(p2src);
     int32_t *d_sched = ws->sched.as<int32_t>();
@@ -616,6 +659,9 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     // accumulate and the full-tile pull: they write other columns of A than the full tiles do.  With
     // profiling everything stays on the caller's stream, so the phase times do not overlap.
     const bool overlap = !ws->profiling;
+    auto zmask_at = [&](int32_t d) -> const uint32_t * {
+        return zany[d] ? reinterpret_cast<const uint32_t *>(d_sched + o_zmask + zoff[d]) : nullptr;
+    };
     if (overlap) PS_CUDA(ws->ensure_side());
     cudaStream_t ss = overlap ? ws->side : st;
     for (int32_t d = Dmax; d >= 0; --d) {
@@ -627,9 +673,12 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
             PS_CUDA(cudaStreamWaitEvent(ss, ws->ev_start, 0));
         }
         if (H > 0) {  // height-2 columns: zero, then push from the grandchildren's gamma
+            // zeroed: the push block, and the inherited columns outside the pulled tiles (the pull writes 0 into
+            // those inside them); inherited columns are pushed after the pull, below
+            const int32_t z0 = hinh[d] > 0 ? dw[d] : h0v[d];
             ph.begin(6);
-            launch_zero_cols(n, A, La, h0v[d], H, ss);
-            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, A, La, h0v[d], ss);
+            launch_zero_cols(n, A, La, z0, rpv[d] - z0, ss);
+            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, A, La, h0v[d], false, ss);
             ph.end();
             launches += 2;
         }
@@ -645,7 +694,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
             ++launches;
             if (d + 2 <= Dmax) {
                 ph.begin(3);
-                launch_scatter_gamma(node_list + node_off[d + 2], ncount[d + 2], t, Bm, Lb, h0v[d], st);
+                launch_scatter_gamma(node_list + node_off[d + 2], ncount[d + 2], t, Bm, Lb, st);
                 ph.end();
                 ++launches;
             }
@@ -670,13 +719,13 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
                 }
                 const int32_t c = 32 * nfull[d];
                 launch_pull(dg, Bm + Lb.base(c), Lb.rpitch(c), 0, 1 << 30, A + La.base(c), La.rpitch(c), 0, 1 << 30, 1,
-                            tail[d], g->tune_bps[tail[d]], ss);
+                            tail[d], g->tune_bps[tail[d]], zmask_at(d) ? zmask_at(d) + nfull[d] : nullptr, ss);
                 ++launches;
             }
             if (nfull[d] > 0) {  // 32-column tiles (or their 16-column halves)
                 const int32_t nt = nfull[d] * (32 / wide);
                 launch_pull(dg, Bm, Lb.rpitch(0), Lb.tile_stride(), Lb.tile_sub(wide), A, La.rpitch(0), La.tile_stride(),
-                            La.tile_sub(wide), nt, wide, g->tune_bps[wide], st);
+                            La.tile_sub(wide), nt, wide, g->tune_bps[wide], zmask_at(d), st);
                 ++launches;
             }
             if (ws->profiling) {
@@ -690,6 +739,12 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         if (overlap && side_work) {  // the gamma of this depth (and every later step) waits for the side work
             PS_CUDA(cudaEventRecord(ws->ev_side, ss));
             PS_CUDA(cudaStreamWaitEvent(st, ws->ev_side, 0));
+        }
+        if (hinh[d] > 0) {  // push nodes in inherited columns: after the pull has written those columns as 0
+            ph.begin(6);
+            launch_push_h2(dg, node_list + node_off[d + 2], ncount[d + 2], t, A, La, h0v[d], true, st);
+            ph.end();
+            ++launches;
         }
         if (d >= 1) {
             ph.begin(7);
@@ -1282,7 +1337,7 @@ probesim_status probesim_autotune(probesim_graph *g, void *stream) {
     for (int32_t T : tiles) {
         float best = 1e30f;
         for (int32_t bps : bpss) {
-            const float ms = time_pull([&] { launch_pull(dg, Da, T, 0, 1, Mb, T, 0, 1, 1, T, bps, st); });
+            const float ms = time_pull([&] { launch_pull(dg, Da, T, 0, 1, Mb, T, 0, 1, 1, T, bps, nullptr, st); });
             if (ms < best) best = ms, g->tune_bps[T] = bps;
         }
     }
@@ -1294,7 +1349,7 @@ probesim_status probesim_autotune(probesim_graph *g, void *stream) {
         for (int32_t bps : bpss) {
             const int32_t nt = 2 * (32 / T);
             const float ms =
-                time_pull([&] { launch_pull(dg, Da, P, 0, 1 << 30, Mb, P, 0, 1 << 30, nt, T, bps, st); });
+                time_pull([&] { launch_pull(dg, Da, P, 0, 1 << 30, Mb, P, 0, 1 << 30, nt, T, bps, nullptr, st); });
             if (ms < best) best = ms, wide_bps[T] = bps;
         }
         per_col[T] = best / 3.0 / 64.0;

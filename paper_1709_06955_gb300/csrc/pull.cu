@@ -59,6 +59,15 @@ __device__ __forceinline__ void vstore(float *p, float v) { __stcs(p, v); }
 __device__ __forceinline__ void vstore(float *p, float2 v) { __stcs(reinterpret_cast<float2 *>(p), v); }
 __device__ __forceinline__ void vstore(float *p, float4 v) { __stcs(reinterpret_cast<float4 *>(p), v); }
 
+// element k of a vector becomes 0 where bit k of b is set
+__device__ __forceinline__ float vmask(float a, uint32_t b) { return (b & 1u) ? 0.f : a; }
+__device__ __forceinline__ float2 vmask(float2 a, uint32_t b) {
+    return make_float2((b & 1u) ? 0.f : a.x, (b & 2u) ? 0.f : a.y);
+}
+__device__ __forceinline__ float4 vmask(float4 a, uint32_t b) {
+    return make_float4((b & 1u) ? 0.f : a.x, (b & 2u) ? 0.f : a.y, (b & 4u) ? 0.f : a.z, (b & 8u) ? 0.f : a.w);
+}
+
 // NCH row gathers of one chunk: in-neighbour j's index sits in lane j % L of the group, slot j / L; past the end
 // of the piece the index is n, the zero spare row
 template <int NCH, int L, int PER, class V, int VEC>
@@ -77,7 +86,7 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
                                               const int32_t *__restrict__ in_col, const float *__restrict__ w,
                                               const float *__restrict__ D, int32_t dpitch, float *__restrict__ MD,
                                               int32_t pitch, int64_t dts, int32_t dsub, int64_t mts, int32_t msub,
-                                              int32_t zrow) {
+                                              int32_t zrow, const uint32_t *__restrict__ zmask) {
     constexpr int VEC = T >= 4 ? 4 : T;
     constexpr int L = T / VEC;         // lanes per group
     constexpr int CH = 8;              // in-neighbours per chunk
@@ -90,6 +99,12 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
     const int64_t mcol0 = (int64_t)(blockIdx.y / msub) * mts + (blockIdx.y % msub) * T + lig * VEC;
     const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / L;
     const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / L;
+    // this lane's columns that are written as 0 (columns a push node inherited: the push fills them later)
+    uint32_t zbits = 0;
+    if (zmask != nullptr) {
+        const int32_t c = blockIdx.y * T + lig * VEC;
+        zbits = (__ldg(zmask + (c >> 5)) >> (c & 31)) & ((1u << VEC) - 1u);
+    }
     // Software pipeline over this group's pieces p, p + ngroups, ...: the metadata of the piece after next and
     // the column indices of the next chunk (or of the next piece's first chunk) are loaded while the current
     // chunk's row gathers are in flight, so a short piece costs about one gather round trip.
@@ -138,7 +153,7 @@ __global__ void __launch_bounds__(256, (T == 32 || T <= 2) ? 4 : 3) k_pull(const
                 if (!more) break;
             }
         }
-        const V res = vscale(acc, wv);
+        const V res = vmask(vscale(acc, wv), zbits);
         float *dst = MD + (int64_t)v * pitch + mcol0;
         if (info < 0) vatomic(dst, res); else vstore(dst, res);
         v = v1, beg = beg1, info = info1;
@@ -157,14 +172,14 @@ int32_t pull_tile_for(int32_t S, int32_t wide) {
 
 void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t dts, int32_t dsub, float *MD,
                  int32_t pitch, int64_t mts, int32_t msub, int32_t ntiles, int32_t tile, int32_t blocks_per_sm,
-                 cudaStream_t s) {
+                 const uint32_t *zmask, cudaStream_t s) {
     if (ntiles <= 0) return;
     const int L = tile >= 4 ? tile / 4 : 1;
     const int64_t threads_needed = g.n_pieces * L;
     const int blocks = grid_for(threads_needed, 256, blocks_per_sm > 0 ? blocks_per_sm : 8);
     dim3 grid(blocks, ntiles);
 #define PS_PULL(T) k_pull<T><<<grid, 256, 0, s>>>(g.piece_v, g.piece_beg, g.piece_len, g.n_pieces, g.in_col, g.w, D, \
-                                                  dpitch, MD, pitch, dts, dsub, mts, msub, g.n)
+                                                  dpitch, MD, pitch, dts, dsub, mts, msub, g.n, zmask)
     switch (tile) {
         case 1: PS_PULL(1); break;
         case 2: PS_PULL(2); break;
