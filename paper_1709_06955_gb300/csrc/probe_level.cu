@@ -266,15 +266,15 @@ void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const i
                        int32_t np1, const int32_t *p2dst, const int4 *p2src, int32_t np2, cudaStream_t s) {
     if (np1 <= 0) return;
     const int32_t pitch = L.K > 0 ? L.K * kGroup : L.R;  // staged row width (a multiple of 4)
-    // staging pays when a stage holds a few rows to spread each part's set-up over; wider rows (batches of
-    // queries) go straight to global memory
+    // staging pays while a row fits two stages of shared memory and the parts are many; rows over 96 KB, and
+    // depths with few parts (a few sectors of each row), are updated in place
     // few parts (deep depths) touch a few sectors of each row: cheaper in place than streaming whole rows
-    if (pitch > 2048 || (int64_t)(np1 + np2) * 40 < pitch) {
+    if ((size_t)pitch * sizeof(float) > 96 * 1024 || (int64_t)(np1 + np2) * 40 < pitch) {
         k_accumulate_direct<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(n, B, L, p1dst, p1src, np1, p2dst,
                                                                              p2src, np2);
         return;
     }
-    // rows per stage: about 32 KB of rows (at least 4); two stages per block (48 KB stages measured slower:
+    // rows per stage: about 32 KB of rows, at least one; two stages per block (48 KB stages measured slower:
     // fewer blocks per SM)
     const int32_t R = std::max<int32_t>(1, std::min<int32_t>(256, 8192 / std::max(1, pitch)));
     const size_t smem = 2 * sizeof(float) * (size_t)R * pitch;
