@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-rates", default="12,60", help="Poisson arrival rates of the serving leg (q/s), comma-separated")
     ap.add_argument("--serve-updates", type=int, default=10000, help="edges per update batch, one batch per 100 ms")
+    ap.add_argument("--serve-plain-rate", type=float, default=60.0,
+                    help="an extra serving window at this rate without updates (0 = none)")
+    ap.add_argument("--serve-workers", type=int, default=3, help="server workers (concurrent batch pipelines)")
+    ap.add_argument("--serve-max-batch", type=int, default=2, help="largest batch a server worker takes")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the serving leg")
     ap.add_argument("--mixed-batch", type=int, default=0,
                     help="queries of the optional mixed-eps top-k leg (eps 0.1 / 0.05 alternating, k = 50); 0 = off")
@@ -165,7 +169,7 @@ def cpu_baseline(n, s, d, qs, budget_s):
                       "queries/s extrapolated from the time per walk" % (k - 1, nr, "%d-node graph" % n, el)}
 
 
-def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, rank):
+def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, rank, workers=3, max_batch=2):
     """For each arrival rate: queries arrive as a Poisson process for `seconds` into a fresh continuous-batching
     server (top-k, k uniform over {10, 50, 100}), while every 100 ms an update batch of updates_per_tick edges
     (half random inserts, half deletes of edges of the original graph) enters the same FIFO.  Returns one
@@ -174,7 +178,7 @@ def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, 
     rng = np.random.default_rng(4 + rank)
     out = []
     for rate in rates:
-        S = probesim.Server(G, workers=2, max_batch=8, kmax=100)
+        S = probesim.Server(G, workers=workers, max_batch=max_batch, kmax=100)
         gaps = rng.exponential(1.0 / rate, size=int(rate * seconds * 3) + 10)
         arrivals = np.cumsum(gaps)
         arrivals = arrivals[arrivals < seconds]
@@ -201,7 +205,7 @@ def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, 
         S.close()
         out.append({"arrival_rate_qps": rate, "queries": int(arrivals.size), "qps": st["qps"], "p50_ms": st["p50_ms"],
                     "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"], "update_batches": st["updates_applied"],
-                    "edges_per_update_tick": updates_per_tick, "workers": 2, "max_batch": 8,
+                    "edges_per_update_tick": updates_per_tick, "workers": workers, "max_batch": max_batch,
                     "k": "uniform {10, 50, 100}", "eps": EPS})
     return out
 
@@ -400,7 +404,11 @@ def run_ours(args):
     # serving leg (last: its update batches change the graph): Poisson arrivals into the continuous-batching
     # server at each rate, with edge-update batches every 100 ms
     rates = [float(r) for r in args.serve_rates.split(",") if r]
-    serving = serving_leg(probesim, G, n, s, d, qs, rates, args.serve_seconds, args.serve_updates, rank)
+    serving = serving_leg(probesim, G, n, s, d, qs, rates, args.serve_seconds, args.serve_updates, rank,
+                          args.serve_workers, args.serve_max_batch)
+    if args.serve_plain_rate > 0:  # the same at a saturating rate without updates: comparable to one per call
+        serving += serving_leg(probesim, G, n, s, d, qs, [args.serve_plain_rate], args.serve_seconds, 0, rank,
+                               args.serve_workers, args.serve_max_batch)
 
     if rank != 0:
         if world > 1:
