@@ -167,8 +167,8 @@ probesim_status probesim_get_stats(const probesim_graph *g, probesim_stats *out)
 typedef struct probesim_server probesim_server;
 
 typedef struct {
-    int32_t workers;            /* concurrent batch pipelines, 1..8 */
-    int32_t max_batch;          /* queries per batch, 1..4096 */
+    int32_t workers;            /* concurrent batch pipelines, 1..8 (default 3) */
+    int32_t max_batch;          /* queries per batch, 1..4096 (default 2) */
     int32_t kmax;               /* largest k a query may ask for, 1..min(4096, n-1) */
     int32_t queue_capacity;     /* queries waiting at once; submit beyond it fails with PROBESIM_E_BUSY */
     double memory_budget_bytes; /* score-buffer memory admitted at once; 0 = 60% of device memory */

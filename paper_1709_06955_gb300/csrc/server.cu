@@ -168,8 +168,10 @@ extern "C" {
 
 probesim_status probesim_server_config_default(probesim_server_config *cfg) {
     if (!cfg) return ps::fail_status(PROBESIM_E_INVALID, "cfg is null");
-    cfg->workers = 2;
-    cfg->max_batch = 16;
+    // measured on R-MAT 2^20 at saturation: several workers overlap one query's host-side schedule with
+    // another's kernels, while wide batches cost more in the accumulate than they save
+    cfg->workers = 3;
+    cfg->max_batch = 2;
     cfg->kmax = 100;
     cfg->queue_capacity = 100000;
     cfg->memory_budget_bytes = 0.0;

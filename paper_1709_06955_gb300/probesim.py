@@ -301,7 +301,7 @@ class Graph:
 class Server:
     """Continuous-batching top-k server over a Graph (probesim_server_*)."""
 
-    def __init__(self, graph, workers=2, max_batch=16, kmax=100, queue_capacity=100000, memory_budget_bytes=0.0):
+    def __init__(self, graph, workers=3, max_batch=2, kmax=100, queue_capacity=100000, memory_budget_bytes=0.0):
         L = load()
         cfg = ServerConfig()
         _check(L.probesim_server_config_default(C.byref(cfg)))
