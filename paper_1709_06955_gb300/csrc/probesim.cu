@@ -915,6 +915,7 @@ static probesim_status run_queries(probesim_graph *g, Workspace *ws, const probe
         }
         return s;
     }
+    if (chunk < nq) g_last_error.clear();  // the budget messages of batches that were split are not errors
     return PROBESIM_OK;
 }
 
