@@ -71,7 +71,7 @@ struct Workspace {
     int profiling = 0;
     std::vector<cudaEvent_t> ev;
     probesim_stats stats{};
-    // a second stream for work of a depth that runs beside the pull (push columns, the tail tile), and the
+    // a second stream for work of a depth that runs beside the pull (the push block, the tail tile), and the
     // events that order it against the caller's stream; created on first use
     cudaStream_t side = nullptr;
     cudaEvent_t ev_start = nullptr, ev_ready = nullptr, ev_side = nullptr;

@@ -89,8 +89,9 @@ struct TrieTable {
     int32_t *query = nullptr;  // query index in the launch
     int32_t *weight = nullptr; // walks sharing the prefix
     int32_t *height = nullptr; // longest path below the node
-    int32_t *slot = nullptr;   // column of the node's score vector at its depth (dense columns first, then
-                               // push columns), -1 if it has none
+    int32_t *slot = nullptr;   // column of the node's score vector at its depth, -1 if it has none: dense
+                               // nodes and push heirs (a push node that took its parent's column) below h0,
+                               // the other push nodes in the push block from h0 on
     float *gamma = nullptr;    // normalised weight minus the excluded score (see probe_level.cu)
     float *G = nullptr;        // sum of the children's gamma
 };

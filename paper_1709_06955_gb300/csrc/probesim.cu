@@ -655,7 +655,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     const int32_t *node_list = ws->node_list.as<int32_t>();
     const int32_t wide = g->tune_wide == 16 ? 16 : 32;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks;
-    // Without profiling, the push columns and the tail tile of a depth run on a second stream beside the
+    // Without profiling, the push block and the tail tile of a depth run on a second stream beside the
     // accumulate and the full-tile pull: they write other columns of A than the full tiles do.  With
     // profiling everything stays on the caller's stream, so the phase times do not overlap.
     const bool overlap = !ws->profiling;
