@@ -23,7 +23,7 @@
  *   orc_topk            the k largest estimates, v != u                      (Def. 2, Sec. 3)
  *   orc_pair_mc         pairwise Monte Carlo meeting estimator              (Sec. 2.2, Eq. 3)
  *
- * Readings of points the paper leaves open (each one is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - the stop test of Def. 3 is applied at every visited node including u_1; a draw x0 below
  *     T_stop = floor((1 - sqrt(c)) * 2^32) stops the walk;
  *   - a walk at a node with no in-neighbour stops there;

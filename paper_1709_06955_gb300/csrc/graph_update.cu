@@ -38,7 +38,7 @@ __device__ __forceinline__ int64_t lower_bound_row(int64_t lo, int64_t hi, uint3
     return lo;
 }
 
-// 1. validity of each batch entry (in-order and out-order copies get the same verdict) and degree deltas
+// 1. validity of each batch entry (in-order and out-order copies get the same decision) and degree deltas
 __global__ void k_upd_mark(DeviceGraph g, UpdateBatch b, long long *in_delta, long long *out_delta) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= b.k) return;
