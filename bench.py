@@ -64,6 +64,23 @@ def dist_env():
     return rank, world, local
 
 
+def replica_query_id(rank, i):
+    """Query id (and Philox key) of the i-th query of a rank: the ranks of a replica run draw disjoint ids."""
+    return rank * 100003 + i
+
+
+def whole_job_rate(local_ms, steps, world, device=None):
+    """Whole-job queries/s of a replica run: every rank timed `steps` queries in `local_ms`; the job's time is
+    the slowest rank's (a max over ranks), and the job processed world * steps queries."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_ms = float(t.item())
+    return world * steps / (local_ms / 1e3), local_ms
+
+
 def measured_peak_hbm():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -260,7 +277,7 @@ def run_ours(args):
     nq = len(qs)
 
     def query(i):
-        j = rank * 100003 + i
+        j = replica_query_id(rank, i)
         return probesim.make_queries([qs[j % nq]], eps=EPS, k=50, query_ids=[j])
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
@@ -294,12 +311,7 @@ def run_ours(args):
         barrier()
         wall = time.perf_counter() - w0
     lat = [a.elapsed_time(b) for a, b in evs]
-    tot_ms = sum(lat)
-    if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1e3)
+    value, tot_ms = whole_job_rate(sum(lat), args.steps, world, dev)
 
     # profiled pass over the first queries again: per-phase CUDA-event times and the pull's own duration
     # (profiling records events around every launch and runs the level loop on one stream)
@@ -327,8 +339,8 @@ def run_ours(args):
     B = max(1, args.batch)
     nb = max(1, args.steps // B)
     outb = torch.zeros((B, n), dtype=torch.float32, device=dev)
-    Qb = [probesim.make_queries([qs[(rank * 100003 + args.warmup + i * B + j) % nq] for j in range(B)], eps=EPS,
-                                query_ids=[rank * 100003 + args.warmup + i * B + j for j in range(B)])
+    Qb = [probesim.make_queries([qs[replica_query_id(rank, args.warmup + i * B + j) % nq] for j in range(B)],
+                                eps=EPS, query_ids=[replica_query_id(rank, args.warmup + i * B + j) for j in range(B)])
           for i in range(nb)]
     G.single_source(Qb[0], out=outb, stream=sptr)
     bev = []
@@ -353,8 +365,8 @@ def run_ours(args):
     if args.mixed_batch > 0:
         MB = args.mixed_batch
         eps_mix = [EPS if j % 2 == 0 else EPS / 2 for j in range(MB)]
-        Qm = probesim.make_queries([qs[(rank * 100003 + 5000 + j) % nq] for j in range(MB)], eps=eps_mix, k=50,
-                                   query_ids=[rank * 100003 + 5000 + j for j in range(MB)])
+        Qm = probesim.make_queries([qs[replica_query_id(rank, 5000 + j) % nq] for j in range(MB)], eps=eps_mix, k=50,
+                                   query_ids=[replica_query_id(rank, 5000 + j) for j in range(MB)])
         mids = torch.empty((MB, 50), dtype=torch.int32, device=dev)
         mvals = torch.empty((MB, 50), dtype=torch.float32, device=dev)
         barrier()
