@@ -148,8 +148,9 @@ probesim_status probesim_set_profiling(probesim_graph *g, int32_t on);
 /* Autotuner of the PROBE level kernel's launch shape on this graph.  It times the pull over the graph's own
  * in-lists for tile widths {1,2,4,8,16,32} columns and {2,4,8,16} blocks per SM (a constant-filled 64-column
  * score matrix, CUDA events, three runs after a warm-up), keeps the fastest shape per width and, for the
- * 32-column tiles of wide matrices, whichever of 32-column tiles and 16-column halves takes less time.  Later queries on the graph use the choice.  Takes about a
- * second; results do not depend on it (only summation order). */
+ * 32-column tiles of wide matrices, whichever of 32-column tiles and 16-column halves takes less time.
+ * Later queries on the graph use the choice.  Takes about a second; results do not depend on it (only the
+ * summation order). */
 probesim_status probesim_autotune(probesim_graph *g, void *stream);
 /* The current choice: *wide_tile in {16, 32}; blocks_per_sm[6] for tile widths 1, 2, 4, 8, 16, 32. */
 probesim_status probesim_get_tuning(const probesim_graph *g, int32_t *wide_tile, int32_t *blocks_per_sm);
