@@ -19,7 +19,9 @@
  *    complete on return either way.
  *  - The library owns the graph and all scratch memory (device memory held by the graph object and
  *    released by probesim_graph_destroy).
- *  - A graph object may be used from several threads; calls on one graph are serialised internally.
+ *  - A graph object may be used from several threads.  Direct query calls on one graph share one workspace
+ *    and are serialised internally; a server's workers each own a workspace and run queries on one graph
+ *    concurrently.  Update batches take the graph store exclusively, between queries.
  *  - All arithmetic on the GPU is FP32 or integer; FP64 is used only on the host (n_r, thresholds).
  */
 #ifndef PROBESIM_H
@@ -39,7 +41,7 @@ typedef enum {
     PROBESIM_E_RANGE = 2,       /* a node id outside [0, n) */
     PROBESIM_E_NOMEM = 3,       /* a device or host allocation failed; the graph is unchanged */
     PROBESIM_E_CUDA = 4,        /* a CUDA runtime error; the message names it */
-    PROBESIM_E_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    PROBESIM_E_TIMEOUT = 5,     /* reserved: no call of this version waits on the device without a bound */
     PROBESIM_E_BUSY = 6,        /* admission refused: not enough free slots or score-buffer memory */
     PROBESIM_E_UNSUPPORTED = 7  /* a valid request this build does not implement */
 } probesim_status;
@@ -132,8 +134,10 @@ typedef struct {
     int64_t edge_gathers;   /* (edge, vector) pairs processed by the PROBE level kernel */
     int64_t probe_launches; /* launches of the PROBE level kernel */
     double probe_ms;        /* their summed CUDA-event duration (profiling on), else 0 */
-    double probe_bytes;     /* algorithmic bytes of those launches: 4 per edge index and 4 per gathered
-                               score per vector-edge, 4 per written score, 12 per vertex per tile */
+    double probe_bytes;     /* algorithmic bytes of those launches: per launch 4 per in-edge index, 16 per
+                               in-list piece record, 4 per vertex weight, and 4 per gathered-row score read
+                               plus 4 per written score for each of the launch's S columns (4m + 16 pieces
+                               + 4n + 8nS) */
     int64_t kernel_launches;/* all kernels this library launched in the call */
     double phase_ms[12];    /* profiling on: CUDA-event time per phase of the deterministic path: 0 walks,
                                1 walk tree and level schedule, 2 D accumulate, 3 gamma scatter, 4 split-row
@@ -194,7 +198,7 @@ typedef struct {
     double qps;          /* completed queries / (last completion - first submit) */
 } probesim_server_stats;
 
-/* workers = 2, max_batch = 16, kmax = 100, queue_capacity = 100000, memory_budget_bytes = 0. */
+/* workers = 3, max_batch = 2, kmax = 100, queue_capacity = 100000, memory_budget_bytes = 0. */
 probesim_status probesim_server_config_default(probesim_server_config *cfg);
 /* Starts the workers over graph g (which must outlive the server). */
 probesim_status probesim_server_create(probesim_graph *g, const probesim_server_config *cfg, probesim_server **out);
@@ -224,7 +228,9 @@ probesim_status probesim_server_destroy(probesim_server *s);
  * and a message naming the limit.  The scratch is one fixed __device__ array of 853,504 bytes in the library,
  * which every GPU that loads the library holds until the process exits.  No call allocates: no cudaMalloc,
  * cudaFree or allocating library routine is used.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first call before any stream capture.
+ * address (cudaGetSymbolAddress) with the device current and loads the top-k kernels; module loading may
+ * allocate device memory, so make that first call before reserving the device's memory for a pool, and before
+ * any stream capture.
  * Every call shares the array, and calls serialise on the host and synchronise `stream` before they return;
  * calls that would overlap on the GPU (for instance from several processes sharing a context) race on it. */
 probesim_status probesim_topk_select_noalloc(const float *scores, int32_t n, int32_t nq, const int32_t *nodes,

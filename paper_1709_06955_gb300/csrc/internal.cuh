@@ -210,6 +210,7 @@ struct TopkScratch {
 int topk_blocks_per_query(int32_t n);
 void launch_topk(int32_t n, int32_t B, const float *scores, const int32_t *qnode, const int32_t *qk, int32_t kmax,
                  TopkScratch sc, int32_t *ids, float *vals, cudaStream_t s, int64_t *launches);
+cudaError_t topk_preload();
 
 // randomized PROBE (rand_probe.cu)
 struct RandLevel {

@@ -213,6 +213,20 @@ __global__ void __launch_bounds__(1024) k_topk_sort(const int32_t *__restrict__ 
     }
 }
 
+// Loads the module that holds the top-k kernels (under lazy loading a module loads, and may allocate device
+// memory, on its first use; querying a kernel's attributes is such a use).
+cudaError_t topk_preload() {
+    const void *fns[] = {(const void *)k_topk_init, (const void *)k_topk_hist, (const void *)k_topk_select,
+                         (const void *)k_topk_collect, (const void *)k_topk_tiebase, (const void *)k_topk_ties,
+                         (const void *)k_topk_sort};
+    for (const void *f : fns) {
+        cudaFuncAttributes a;
+        const cudaError_t e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 void launch_topk(int32_t n, int32_t B, const float *scores, const int32_t *qnode, const int32_t *qk, int32_t kmax,
                  TopkScratch sc, int32_t *ids, float *vals, cudaStream_t s, int64_t *launches) {
     const int nblk = topk_blocks_per_query(n);

@@ -67,12 +67,16 @@ extern "C" probesim_status probesim_topk_select_noalloc(const float *scores, int
         cudaGetLastError();
         return err(PROBESIM_E_CUDA, "cudaGetDevice failed");
     }
-    if (!g_addr[dev]) {  // once per device, with that device current: the device address of the array
-        void *p = nullptr;
+    if (!g_addr[dev]) {  // once per device, with that device current: the device address of the array,
+        void *p = nullptr;   // and the top-k kernels loaded (module loads may allocate; later calls do not)
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return err(PROBESIM_E_CUDA, "cudaGetSymbolAddress of the scratch array failed");
+        }
+        if (ps::topk_preload() != cudaSuccess) {
+            cudaGetLastError();
+            return err(PROBESIM_E_CUDA, "loading the top-k kernels failed");
         }
         g_addr[dev] = p;
     }

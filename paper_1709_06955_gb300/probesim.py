@@ -187,9 +187,20 @@ def topk_select_noalloc(scores, nodes, ks, kmax, ids, vals, stream=None):
     For callers that cannot allocate device memory while they run.  ``scores`` is a CUDA tensor [nq, n];
     ``ids`` / ``vals`` are CUDA tensors [nq, kmax] (int32 / float32) that receive the results; ``nodes`` and
     ``ks`` are host sequences of length nq.  At most 64 queries and kmax <= 1024 per call."""
+    import torch
+    if not (_is_torch(scores) and scores.dtype == torch.float32 and scores.dim() == 2):
+        raise ValueError("scores must be a 2-d float32 tensor [nq, n]")
     nq, n = int(scores.shape[0]), int(scores.shape[1])
-    nodes = np.ascontiguousarray(nodes, dtype=np.int32)
-    ks = np.ascontiguousarray(ks, dtype=np.int32)
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32).ravel()
+    ks = np.ascontiguousarray(ks, dtype=np.int32).ravel()
+    if nodes.size != nq or ks.size != nq:
+        raise ValueError("nodes and ks must hold one entry per score row (%d)" % nq)
+    for name, t, dt in (("ids", ids, torch.int32), ("vals", vals, torch.float32)):
+        if not (_is_torch(t) and t.dtype == dt and tuple(t.shape) == (nq, int(kmax))):
+            raise ValueError("%s must be a %s tensor of shape (%d, %d)" % (name, dt, nq, int(kmax)))
+    for name, t in (("scores", scores), ("ids", ids), ("vals", vals)):
+        if not t.is_cuda or t.device != scores.device:
+            raise ValueError("%s must be CUDA memory on one device" % name)
     _check(load().probesim_topk_select_noalloc(_ptr(scores), n, nq, _ptr(nodes), _ptr(ks), int(kmax), _ptr(ids),
                                                _ptr(vals), _stream(stream)))
     return ids, vals

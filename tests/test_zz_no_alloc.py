@@ -41,7 +41,12 @@ def test_noalloc_topk_matches_topk_on_two_calls(setup):
     for call in range(2):
         ids = torch.full((6, 100), -7, dtype=torch.int32, device="cuda")
         vals = torch.full((6, 100), -7.0, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         probesim.topk_select_noalloc(scores, qs, ks, 100, ids, vals)
+        free1 = torch.cuda.mem_get_info()[0]
+        if call == 1:  # after the first call's set-up, a call takes no device memory
+            assert free1 == free0
         ids, vals = ids.cpu().numpy(), vals.cpu().numpy()
         for i in range(6):
             k = ks[i]
