@@ -34,9 +34,10 @@
  *   - level j of PROBE on (u_1..u_i) excludes u_{i-j-1};
  *   - Pruning Rule 2 drops x when Score(x) * sqrt(c)^(i-j-1) <= eps_p, and eps_p = 0 disables it;
  *   - in the switch of Sec. 4.4 a probe of weight w whose frontier H_j has out-degree sum above
- *     c0 * w * n continues as w randomized instances (one per walk sharing the prefix) that start
- *     from the deterministic H_j and carry its scores (a member keeps the score of the in-neighbour
- *     it sampled); with all scores 1 this is exactly Alg. 3.
+ *     c0 * w * n is handed to the randomized PROBE algorithm: the deterministic levels run so far are
+ *     dropped and Alg. 3 runs on the whole partial walk w times, once per walk sharing the prefix,
+ *     each with that walk's own Philox stream (Sec. 4.4 states that the switched probe needs w
+ *     independent randomized probes, averaged).
  */
 #include <math.h>
 #include <stdint.h>
@@ -474,13 +475,13 @@ int orc_single_source_batch(const orc_graph *g, int32_t u, const orc_params *p, 
                 int64_t degsum = 0;
                 for (int32_t s = 0; s < hj->size; ++s) degsum += orc_out_degree(g, hj->member[s]);
                 if (p->probe_mode == 1 || (double)degsum > p->c0 * wq * (double)g->n) {
-                    /* Sec. 4.4: continue as one randomized instance per walk sharing this prefix,
-                     * each starting from the current H_j */
+                    /* Sec. 4.4: the probe switches to the randomized PROBE algorithm (Alg. 3) on the
+                     * partial walk (r_1.node .. r_q.node), run once for each of the w walks sharing it */
                     for (int32_t l = T[t].walk_head; l >= 0; l = walk_next[l]) {
                         orc_set *ra = &rw.a, *rb = &rw.b;
                         orc_set_clear(ra);
-                        for (int32_t s = 0; s < hj->size; ++s) orc_set_put(ra, hj->member[s], hj->score[hj->member[s]]);
-                        for (int32_t jj = j; jj <= q - 2; ++jj) {
+                        orc_set_put(ra, prefix[q - 1], 1.0); /* Alg. 3 line 2: H_0 = {(u_q, 1)} */
+                        for (int32_t jj = 0; jj <= q - 2; ++jj) {
                             orc_rand_level(g, p->c, p->seed, p->query_id, (uint32_t)walk_id[l], q, jj, ra,
                                            prefix[q - jj - 2], rb, &rw.t, cnt);
                             orc_set *tmp = ra; ra = rb; rb = tmp;
