@@ -145,9 +145,20 @@ typedef struct {
                                host wall-clock time of the column schedule, during which the device waits;
                                10-11 unused */
     int64_t max_columns;    /* widest score matrix of the level loop, in columns (deterministic path) */
+    int64_t probes;         /* walk prefixes probed one by one (Pruning Rule 2 or the switch) */
+    int64_t switched;       /* of those, the probes the switch of Sec. 4.4 handed to Alg. 3 */
+    int64_t table_passes;   /* passes over the frontier engine's per-level tables (more than one per level when
+                               a table exceeds a quarter of the memory budget) */
+    int64_t max_table_slots;/* largest per-level table, in slots of 12 bytes */
 } probesim_stats;
 
 probesim_status probesim_set_profiling(probesim_graph *g, int32_t on);
+
+/* Device memory that one call's working buffers on this graph may take, in bytes (0 restores the default, 60%
+ * of the device's memory at graph creation).  A call whose queries need more is cut into smaller batches; the
+ * frontier engine (Pruning Rule 2, the switch) also cuts a level's table into passes of a quarter of it.  A
+ * single query that still does not fit fails with PROBESIM_E_NOMEM.  Results do not depend on the budget. */
+probesim_status probesim_set_memory_budget(probesim_graph *g, double bytes);
 
 /* Autotuner of the PROBE level kernel's launch shape on this graph.  It times the pull over the graph's own
  * in-lists for tile widths {1,2,4,8,16,32} columns and {2,4,8,16} blocks per SM (a constant-filled 64-column

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <shared_mutex>
 #include <string>
@@ -66,6 +67,9 @@ struct Workspace {
     DevBuf md_a, md_b, out_stage;                       // the two score buffers; host-output staging
     DevBuf r_cnt, r_off, r_part, r_iwalk, r_ilen, r_iq, r_ik, r_fi[2], r_fn[2], r_keys[2], r_deg, r_pref, r_counts, r_ctr;
     DevBuf tk_hist, tk_state, tk_tie, tk_cid, tk_cval, tk_ids, tk_vals, tk_qk;
+    // frontier engine: walk-prefix slots, switched flags, probes, frontier lists, next-level table, estimates
+    DevBuf f_wslot, f_tsw, f_slot, f_misc, f_anc, f_deg, f_state, f_rsize, f_roff, f_acc, f_tab, f_work, f_wp,
+        f_lp[2], f_lx[2], f_lv[2], f_cuts, f_keys, f_vals, f_bcnt, f_bpre;
     PinnedBuf pin_q;  // query arrays of one batch
     PinnedBuf pin_s;  // counters and schedule offsets (fixed size, allocated at creation)
     int profiling = 0;
@@ -89,7 +93,9 @@ struct Workspace {
                           &sched, &md_a, &md_b, &out_stage, &r_cnt, &r_off,
                           &r_part, &r_iwalk, &r_ilen, &r_iq, &r_ik, &r_fi[0], &r_fi[1], &r_fn[0], &r_fn[1],
                           &r_keys[0], &r_keys[1], &r_deg, &r_pref, &r_counts, &r_ctr, &tk_hist, &tk_state, &tk_tie,
-                          &tk_cid, &tk_cval, &tk_ids, &tk_vals, &tk_qk};
+                          &tk_cid, &tk_cval, &tk_ids, &tk_vals, &tk_qk, &f_wslot, &f_tsw, &f_slot, &f_misc, &f_anc,
+                          &f_deg, &f_state, &f_rsize, &f_roff, &f_acc, &f_tab, &f_work, &f_wp, &f_lp[0], &f_lp[1],
+                          &f_lx[0], &f_lx[1], &f_lv[0], &f_lv[1], &f_cuts, &f_keys, &f_vals, &f_bcnt, &f_bpre};
         for (DevBuf *b : bufs) b->release();
         pin_q.release();
         pin_s.release();
@@ -118,7 +124,8 @@ struct probesim_graph {
     DevBuf u_batch, u_valid, u_vpre, u_delta, u_deg, u_part, u_hist;
     uint64_t epoch = 0;
     Workspace ws0;
-    size_t budget = 0;
+    std::atomic<size_t> budget{0};  // device memory one call's working buffers may take (set while calls run)
+    size_t budget0 = 0;  // the default: 60% of device memory at creation
     // pull launch shape chosen by probesim_autotune (defaults until then)
     int32_t tune_wide = 32;       // widest tile (16 or 32 columns)
     int32_t tune_bps[33] = {0};   // blocks per SM per tile width (0 = default 8)

@@ -94,6 +94,7 @@ struct TrieTable {
                                // the other push nodes in the push block from h0 on
     float *gamma = nullptr;    // normalised weight minus the excluded score (see probe_level.cu)
     float *G = nullptr;        // sum of the children's gamma
+    int32_t *walk_slot = nullptr;  // optional [W][l_max]: slot of the prefix of length i of walk w at [w][i-1]
 };
 
 constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
@@ -212,6 +213,55 @@ void launch_topk(int32_t n, int32_t B, const float *scores, const int32_t *qnode
                  TopkScratch sc, int32_t *ids, float *vals, cudaStream_t s, int64_t *launches);
 cudaError_t topk_preload();
 
+// frontier PROBE engine (frontier.cu): each walk prefix probed on its own, with Pruning Rule 2 and the switch
+constexpr int kFixShift = 44;  // scores and estimates accumulate as int64 multiples of 2^-44
+constexpr int32_t kProbeSwitched = 1, kProbeDense = 2;
+constexpr int64_t kFrontierMaxWalks = (int64_t)1 << 18;  // per query: keeps every fixed-point sum below 2^62
+struct FrontierProbes {
+    int32_t P = 0;
+    int32_t *slot = nullptr;              // tree slot of the probed prefix
+    int32_t *anc = nullptr;               // tree slot of the node the current level excludes
+    unsigned long long *deg = nullptr;    // out-degree sum of the current level's kept entries
+    int32_t *state = nullptr;             // kProbeSwitched | kProbeDense
+    long long *rsize = nullptr;           // region slots in the next level's table
+    long long *roff = nullptr;            // [P+1] region offsets (exclusive prefix sums of rsize)
+};
+struct FrontierList {  // entries of the frontiers, grouped by probe in probe order
+    int32_t *p = nullptr;
+    int32_t *x = nullptr;
+    long long *val = nullptr;             // score in 2^-44 units
+};
+struct FrontierExpand {
+    const long long *wp = nullptr;        // [nF+1] prefix sums of the entries' work (out-degrees)
+    int64_t f_lo = 0, f_hi = 0;           // entries of this pass
+    long long e_lo = 0, e_hi = 0;         // work items of this pass
+    int32_t j = 0;                        // level
+    int32_t *keys = nullptr;              // next level's table: node per slot, -1 empty
+    unsigned long long *vals = nullptr;   // score per slot (2^-44 units)
+    long long rbase = 0;                  // table offset of this pass's first region
+    unsigned long long *acc = nullptr;    // [B][n] estimates (2^-44 units, internal ids)
+    int32_t n = 0;
+};
+void launch_fr_list(TrieTable t, int32_t *slot, int32_t *count, cudaStream_t s);
+void launch_fr_init(TrieTable t, FrontierProbes P, FrontierList F, cudaStream_t s);
+void launch_fr_prune(FrontierList F, int64_t nF, TrieTable t, FrontierProbes P, const int64_t *out_off, const float *pw,
+                     float eps_p, int32_t j, long long *work, cudaStream_t s);
+void launch_fr_regions(TrieTable t, FrontierProbes P, int32_t j, int32_t n, const long long *thr, uint8_t *t_sw,
+                       unsigned long long *ctr, cudaStream_t s);
+void launch_fr_work(FrontierList F, int64_t nF, FrontierProbes P, long long *work, cudaStream_t s);
+void launch_fr_expand(const DeviceGraph &g, TrieTable t, FrontierProbes P, FrontierList F, const FrontierExpand &a,
+                      cudaStream_t s);
+int64_t fr_compact_blocks(long long T);
+void launch_fr_count(const int32_t *keys, long long T, long long *bcount, cudaStream_t s);
+void launch_fr_write(const int32_t *keys, const unsigned long long *vals, long long T, const long long *roff, int32_t p0,
+                     int32_t p1, long long rbase, const long long *bpre, FrontierList out, long long out_base,
+                     long long out_cap, cudaStream_t s);
+void launch_fr_advance(TrieTable t, FrontierProbes P, cudaStream_t s);
+void launch_fr_bounds(const int32_t *fp, int64_t nF, const long long *wp, const int32_t *probes, int32_t count,
+                      long long *out, cudaStream_t s);
+void launch_fr_finalize(int32_t n, int32_t B, const int32_t *qnode, const unsigned long long *acc, const int32_t *counts,
+                        const float *inv_nr, const int32_t *ext2int, float *out, cudaStream_t s);
+
 // randomized PROBE (rand_probe.cu)
 struct RandLevel {
     const int32_t *fr_inst = nullptr, *fr_node = nullptr;  // frontier H_j (entries with out-edges)
@@ -230,12 +280,15 @@ struct RandLevel {
 };
 int64_t scan64_partials_needed(int64_t count);
 void launch_scan64(const long long *in, int64_t count, long long *partial, long long *out, cudaStream_t s);
-void launch_inst_count(const int32_t *lens, int32_t W, long long *cnt, cudaStream_t s);
+// Instances (walk w, prefix length i), i = 2..len; with walk_slot and t_sw given, only those whose prefix's tree
+// slot is flagged in t_sw (the probes the switch of Sec. 4.4 handed to Alg. 3).
+void launch_inst_count(const int32_t *lens, int32_t W, long long *cnt, const int32_t *walk_slot, const uint8_t *t_sw,
+                       int32_t l_max, cudaStream_t s);
 void launch_inst_init(const QueryBatch &q, const DeviceGraph &g, const int32_t *lens, int32_t W, int32_t l_max,
                       const int32_t *walks, const long long *inst_off, int32_t *inst_walk, int32_t *inst_len,
                       int32_t *inst_q, uint32_t *inst_k, int32_t *fr_inst, int32_t *fr_node,
                       unsigned long long *fr_count, unsigned long long *keys, int64_t cap, int32_t *overflow,
-                      cudaStream_t s);
+                      const int32_t *walk_slot, const uint8_t *t_sw, cudaStream_t s);
 void launch_frontier_degree(const int32_t *fr_inst, const int32_t *fr_node, int64_t F, const int32_t *inst_len, int32_t j,
                             const int64_t *out_off, long long *deg, cudaStream_t s);
 void launch_rand_level(const DeviceGraph &g, const int32_t *walks, int32_t l_max, const int32_t *inst_walk,

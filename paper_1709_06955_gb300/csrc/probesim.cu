@@ -774,64 +774,70 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     return PROBESIM_OK;
 }
 
-// Randomized PROBE (Alg. 3) for every probe of Alg. 1: one instance per (walk, prefix length), run level by
-// level over hash-set frontiers; the estimate is the member count of the final levels divided by n_r.
-static probesim_status run_batch_rand(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t B,
-                                      float *d_out, cudaStream_t st, bool *too_big) {
-    *too_big = false;
-    const DeviceGraph &dg = g->dg;
-    const int32_t n = dg.n, L = g->cfg.l_max;
-    BatchPlan P;
-    PS_TRY(plan_batch(g, q, B, P));
-    QueryBatch qb;
+// Walks of a planned batch (Def. 3): uploads the queries, launches the walk kernel and reads back the walk
+// node count and the longest walk.
+static probesim_status batch_walks(probesim_graph *g, Workspace *ws, const BatchPlan &P, QueryBatch &qb,
+                                   int64_t *walk_nodes, int32_t *max_len, int64_t &launches, cudaStream_t st) {
+    const int32_t L = g->cfg.l_max;
     PS_TRY(upload_batch(ws, P, qb, st));
-    int64_t launches = 0;
-    const int32_t W = P.W;
-    PS_CUDA(ws->walks.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)W * L)));
-    PS_CUDA(ws->lens.ensure(sizeof(int32_t) * std::max<int32_t>(1, W)));
+    PS_CUDA(ws->walks.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)P.W * L)));
+    PS_CUDA(ws->lens.ensure(sizeof(int32_t) * std::max<int32_t>(1, P.W)));
     PS_CUDA(ws->ctr.ensure(sizeof(LaunchCounters)));
     LaunchCounters *d_ctr = ws->ctr.as<LaunchCounters>();
     PS_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(LaunchCounters), st));
-    launch_walks(dg, qb, W, L, g->t_stop, g->cfg.seed, ws->walks.as<int32_t>(), ws->lens.as<int32_t>(), false, d_ctr, st);
+    launch_walks(g->dg, qb, P.W, L, g->t_stop, g->cfg.seed, ws->walks.as<int32_t>(), ws->lens.as<int32_t>(), false,
+                 d_ctr, st);
     ++launches;
-    // instances: one per (walk, i), i = 2..len
+    LaunchCounters *h_ctr = ws->pin_s.as<LaunchCounters>();
+    PS_CUDA(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(LaunchCounters), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    *walk_nodes = (int64_t)h_ctr->walk_nodes;
+    *max_len = h_ctr->max_len;
+    ws->stats.walks += P.W;
+    ws->stats.walk_nodes += *walk_nodes;
+    return PROBESIM_OK;
+}
+
+// Randomized PROBE (Alg. 3) instances, one per (walk, prefix length i >= 2) -- or, with walk_slot and t_sw, only
+// those whose prefix's tree slot is flagged -- run level by level over hash-set frontiers.  Leaves the member
+// counts of the final levels in ws->r_counts ([B][n], internal ids).
+static probesim_status rand_instances(probesim_graph *g, Workspace *ws, const QueryBatch &qb, int32_t B, int32_t W,
+                                      int32_t max_len, const int32_t *walk_slot, const uint8_t *t_sw, int64_t &launches,
+                                      cudaStream_t st) {
+    const DeviceGraph &dg = g->dg;
+    const int32_t n = dg.n, L = g->cfg.l_max;
     PS_CUDA(ws->r_cnt.ensure(sizeof(long long) * std::max(1, W)));
     PS_CUDA(ws->r_off.ensure(sizeof(long long) * (W + 1)));
     PS_CUDA(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(W)));
-    launch_inst_count(ws->lens.as<int32_t>(), W, ws->r_cnt.as<long long>(), st);
+    launch_inst_count(ws->lens.as<int32_t>(), W, ws->r_cnt.as<long long>(), walk_slot, t_sw, L, st);
     launch_scan64(ws->r_cnt.as<long long>(), W, ws->r_part.as<long long>(), ws->r_off.as<long long>(), st);
     launches += 4;
     long long *h_ll = reinterpret_cast<long long *>(ws->pin_s.as<char>() + 32768);
-    LaunchCounters *h_ctr = ws->pin_s.as<LaunchCounters>();
     PS_CUDA(cudaMemcpyAsync(h_ll, ws->r_off.as<long long>() + W, sizeof(long long), cudaMemcpyDeviceToHost, st));
-    PS_CUDA(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(LaunchCounters), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     const int64_t NI = h_ll[0];
-    const int32_t max_len = h_ctr->max_len;
-    ws->stats.walks += W;
-    ws->stats.walk_nodes += (int64_t)h_ctr->walk_nodes;
     if (NI >= ((int64_t)1 << 31)) return fail(PROBESIM_E_INVALID, "too many probe instances in one call");
-    PS_CUDA(ws->r_iwalk.ensure(sizeof(int32_t) * std::max<int64_t>(1, NI)));
-    PS_CUDA(ws->r_ilen.ensure(sizeof(int32_t) * std::max<int64_t>(1, NI)));
-    PS_CUDA(ws->r_iq.ensure(sizeof(int32_t) * std::max<int64_t>(1, NI)));
-    PS_CUDA(ws->r_ik.ensure(sizeof(uint32_t) * std::max<int64_t>(1, NI)));
     PS_CUDA(ws->r_counts.ensure(sizeof(int32_t) * (size_t)B * n));
     PS_CUDA(cudaMemsetAsync(ws->r_counts.p, 0, sizeof(int32_t) * (size_t)B * n, st));
+    if (NI == 0) return PROBESIM_OK;
+    PS_CUDA(ws->r_iwalk.ensure(sizeof(int32_t) * NI));
+    PS_CUDA(ws->r_ilen.ensure(sizeof(int32_t) * NI));
+    PS_CUDA(ws->r_iq.ensure(sizeof(int32_t) * NI));
+    PS_CUDA(ws->r_ik.ensure(sizeof(uint32_t) * NI));
     PS_CUDA(ws->r_ctr.ensure(sizeof(unsigned long long) * 4));
     unsigned long long *d_fc = ws->r_ctr.as<unsigned long long>();
     int32_t *d_over = reinterpret_cast<int32_t *>(d_fc + 2);
     int cur = 0;
     int64_t cap = next_pow2(std::max<int64_t>(1024, 2 * NI));
-    int64_t fcap = std::max<int64_t>(1, NI);
     PS_CUDA(ws->r_keys[cur].ensure(8 * (size_t)cap));
-    PS_CUDA(ws->r_fi[cur].ensure(4 * (size_t)fcap));
-    PS_CUDA(ws->r_fn[cur].ensure(4 * (size_t)fcap));
+    PS_CUDA(ws->r_fi[cur].ensure(4 * (size_t)NI));
+    PS_CUDA(ws->r_fn[cur].ensure(4 * (size_t)NI));
     PS_CUDA(cudaMemsetAsync(ws->r_keys[cur].p, 0xFF, 8 * (size_t)cap, st));
     PS_CUDA(cudaMemsetAsync(d_fc, 0, sizeof(unsigned long long) * 4, st));
     launch_inst_init(qb, dg, ws->lens.as<int32_t>(), W, L, ws->walks.as<int32_t>(), ws->r_off.as<long long>(),
                      ws->r_iwalk.as<int32_t>(), ws->r_ilen.as<int32_t>(), ws->r_iq.as<int32_t>(), ws->r_ik.as<uint32_t>(),
                      ws->r_fi[cur].as<int32_t>(), ws->r_fn[cur].as<int32_t>(), d_fc, ws->r_keys[cur].as<unsigned long long>(),
-                     cap, d_over, st);
+                     cap, d_over, walk_slot, t_sw, st);
     ++launches;
     PS_CUDA(cudaMemcpyAsync(h_ll, d_fc, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
@@ -886,7 +892,279 @@ static probesim_status run_batch_rand(probesim_graph *g, Workspace *ws, const pr
         cur_cap = ncap;
         ws->stats.levels += 1;
     }
-    launch_rand_finalize(n, B, qb.node, ws->r_counts.as<int32_t>(), qb.inv_nr, dg.ext2int, d_out, st);
+    return PROBESIM_OK;
+}
+
+// Randomized PROBE (Alg. 3) for every probe of Alg. 1: one instance per (walk, prefix length); the estimate is
+// the member count of the final levels divided by n_r.
+static probesim_status run_batch_rand(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t B,
+                                      float *d_out, cudaStream_t st, bool *too_big) {
+    *too_big = false;
+    BatchPlan P;
+    PS_TRY(plan_batch(g, q, B, P));
+    QueryBatch qb;
+    int64_t launches = 0, walk_nodes = 0;
+    int32_t max_len = 0;
+    PS_TRY(batch_walks(g, ws, P, qb, &walk_nodes, &max_len, launches, st));
+    PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, nullptr, nullptr, launches, st));
+    launch_rand_finalize(g->dg.n, B, qb.node, ws->r_counts.as<int32_t>(), qb.inv_nr, g->dg.ext2int, d_out, st);
+    ++launches;
+    PS_CUDA(cudaGetLastError());
+    PS_CUDA(cudaStreamSynchronize(st));
+    ws->stats.kernel_launches += launches;
+    return PROBESIM_OK;
+}
+
+// Frontier engine (frontier.cu): every prefix of the batch's walk trees probed on its own with Pruning Rule 2,
+// and, in PROBESIM_PROBE_SWITCH mode, the switch of Sec. 4.4 handing large probes to Alg. 3.
+static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t B,
+                                          float *d_out, cudaStream_t st, bool *too_big) {
+    *too_big = false;
+    const DeviceGraph &dg = g->dg;
+    const int32_t n = dg.n, L = g->cfg.l_max;
+    const bool sw_mode = g->cfg.probe_mode == PROBESIM_PROBE_SWITCH;
+    BatchPlan P;
+    PS_TRY(plan_batch(g, q, B, P));
+    int64_t max_w = 1;
+    for (int32_t b = 0; b < B; ++b) {
+        if (num_walks(g->cfg.c, q[b].eps, g->cfg.delta, n) > kFrontierMaxWalks)
+            return fail(PROBESIM_E_INVALID, "eps too small: Pruning Rule 2 and the switch take at most 2^18 walks per query");
+        max_w = std::max<int64_t>(max_w, P.base[b + 1] - P.base[b]);
+    }
+    if ((size_t)P.W * L * 8 > g->budget / 4 && B > 1) {
+        *too_big = true;
+        return PROBESIM_E_NOMEM;
+    }
+    QueryBatch qb;
+    int64_t launches = 0, walk_nodes = 0;
+    int32_t max_len = 0;
+    PS_TRY(batch_walks(g, ws, P, qb, &walk_nodes, &max_len, launches, st));
+    // reverse-reachability tree (Alg. 4) with the slot of every walk prefix
+    TrieTable t;
+    t.cap = next_pow2(std::max<int64_t>(1024, 2 * (walk_nodes + B) + 64));
+    const size_t cap = (size_t)t.cap;
+    PS_CUDA(ws->t_key.ensure(8 * cap));
+    PS_CUDA(ws->t_node.ensure(4 * cap));
+    PS_CUDA(ws->t_parent.ensure(4 * cap));
+    PS_CUDA(ws->t_depth.ensure(4 * cap));
+    PS_CUDA(ws->t_query.ensure(4 * cap));
+    PS_CUDA(ws->t_weight.ensure(4 * cap));
+    PS_CUDA(ws->t_height.ensure(4 * cap));
+    PS_CUDA(ws->f_wslot.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)P.W * L)));
+    PS_CUDA(ws->f_tsw.ensure(cap));
+    t.key = ws->t_key.as<unsigned long long>();
+    t.node = ws->t_node.as<int32_t>();
+    t.parent = ws->t_parent.as<int32_t>();
+    t.depth = ws->t_depth.as<int32_t>();
+    t.query = ws->t_query.as<int32_t>();
+    t.weight = ws->t_weight.as<int32_t>();
+    t.height = ws->t_height.as<int32_t>();
+    t.walk_slot = ws->f_wslot.as<int32_t>();
+    uint8_t *t_sw = ws->f_tsw.as<uint8_t>();
+    PS_CUDA(cudaMemsetAsync(t.key, 0xFF, 8 * cap, st));
+    PS_CUDA(cudaMemsetAsync(t.weight, 0, 4 * cap, st));
+    PS_CUDA(cudaMemsetAsync(t.height, 0, 4 * cap, st));
+    PS_CUDA(cudaMemsetAsync(t_sw, 0, cap, st));
+    LaunchCounters *d_ctr = ws->ctr.as<LaunchCounters>();
+    launch_trie_insert(dg, qb, P.W, L, ws->walks.as<int32_t>(), ws->lens.as<int32_t>(), t, d_ctr, st);
+    // the probes: tree nodes of depth >= 2
+    PS_CUDA(ws->f_slot.ensure(sizeof(int32_t) * std::max<int64_t>(1, walk_nodes)));
+    PS_CUDA(ws->f_misc.ensure(64));
+    int32_t *d_np = ws->f_misc.as<int32_t>();
+    unsigned long long *d_fctr = reinterpret_cast<unsigned long long *>(ws->f_misc.as<char>() + 8);
+    PS_CUDA(cudaMemsetAsync(d_np, 0, 64, st));
+    launch_fr_list(t, ws->f_slot.as<int32_t>(), d_np, st);
+    launches += 2;
+    LaunchCounters *h_ctr = ws->pin_s.as<LaunchCounters>();
+    long long *h_ll = reinterpret_cast<long long *>(ws->pin_s.as<char>() + 32768);
+    PS_CUDA(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(LaunchCounters), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(h_ll, d_np, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    if (h_ctr->overflow) return fail(PROBESIM_E_CUDA, "internal: walk tree table overflow");
+    const int32_t NP = reinterpret_cast<int32_t *>(h_ll)[0];
+    ws->stats.probes += NP;
+    ws->stats.tree_nodes += NP;
+    // per-probe state, the two frontier lists, the estimate sums
+    FrontierProbes PR;
+    PR.P = NP;
+    PS_CUDA(ws->f_anc.ensure(sizeof(int32_t) * std::max(1, NP)));
+    PS_CUDA(ws->f_deg.ensure(sizeof(unsigned long long) * std::max(1, NP)));
+    PS_CUDA(ws->f_state.ensure(sizeof(int32_t) * std::max(1, NP)));
+    PS_CUDA(ws->f_rsize.ensure(sizeof(long long) * (NP + 1)));
+    PS_CUDA(ws->f_roff.ensure(sizeof(long long) * (NP + 1)));
+    PR.slot = ws->f_slot.as<int32_t>();
+    PR.anc = ws->f_anc.as<int32_t>();
+    PR.deg = ws->f_deg.as<unsigned long long>();
+    PR.state = ws->f_state.as<int32_t>();
+    PR.rsize = ws->f_rsize.as<long long>();
+    PR.roff = ws->f_roff.as<long long>();
+    const size_t accn = (size_t)B * n;
+    PS_CUDA(ws->f_acc.ensure(sizeof(unsigned long long) * accn));
+    PS_CUDA(cudaMemsetAsync(ws->f_acc.p, 0, sizeof(unsigned long long) * accn, st));
+    // host tables: thr[w] = floor(c0 * w * n) in FP64 (the switch compares the integer out-degree sum with it),
+    // pw[k] = sqrt(c)^k rounded to FP32 (Rule 2's factor)
+    const size_t nthr = sw_mode ? (size_t)max_w + 1 : 0;
+    const size_t tab_bytes = 256 * sizeof(float) + nthr * sizeof(long long);
+    PS_CUDA(ws->f_tab.ensure(tab_bytes));
+    PS_CUDA(ws->pin_q.ensure(tab_bytes));
+    {
+        char *h = ws->pin_q.as<char>();
+        float *pw = reinterpret_cast<float *>(h);
+        const double sc = std::sqrt(g->cfg.c);
+        for (int k = 0; k < 256; ++k) pw[k] = (float)std::pow(sc, (double)k);
+        long long *thr = reinterpret_cast<long long *>(h + 256 * sizeof(float));
+        for (size_t w = 0; w < nthr; ++w) {
+            const double x = std::floor((double)g->cfg.c0 * (double)w * (double)n);
+            thr[w] = x >= 9.0e18 ? (long long)9000000000000000000ll : (long long)x;
+        }
+        PS_CUDA(cudaMemcpyAsync(ws->f_tab.p, h, tab_bytes, cudaMemcpyHostToDevice, st));
+    }
+    const float *d_pw = ws->f_tab.as<float>();
+    const long long *d_thr = sw_mode ? reinterpret_cast<const long long *>(ws->f_tab.as<char>() + 256 * sizeof(float)) : nullptr;
+    int cur = 0;
+    int64_t nF = NP;
+    PS_CUDA(ws->f_lp[cur].ensure(sizeof(int32_t) * std::max<int64_t>(1, nF)));
+    PS_CUDA(ws->f_lx[cur].ensure(sizeof(int32_t) * std::max<int64_t>(1, nF)));
+    PS_CUDA(ws->f_lv[cur].ensure(sizeof(long long) * std::max<int64_t>(1, nF)));
+    auto list_of = [&](int k) {
+        FrontierList F;
+        F.p = ws->f_lp[k].as<int32_t>();
+        F.x = ws->f_lx[k].as<int32_t>();
+        F.val = ws->f_lv[k].as<long long>();
+        return F;
+    };
+    launch_fr_init(t, PR, list_of(cur), st);
+    ++launches;
+    // the next level's table is cut into passes of at most this many slots (12 bytes each)
+    const long long pass_slots = std::max<long long>((long long)n, (long long)(g->budget / 4 / 12));
+    int64_t switched = 0;
+    for (int32_t j = 0; nF > 0; ++j) {
+        const FrontierList F = list_of(cur);
+        PS_CUDA(ws->f_work.ensure(sizeof(long long) * (nF + 1)));
+        PS_CUDA(ws->f_wp.ensure(sizeof(long long) * (nF + 1)));
+        PS_CUDA(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(nF, NP))));
+        long long *work = ws->f_work.as<long long>(), *wp = ws->f_wp.as<long long>();
+        PS_CUDA(cudaMemsetAsync(d_fctr, 0, 2 * sizeof(unsigned long long), st));
+        launch_fr_prune(F, nF, t, PR, dg.out_off, d_pw, g->cfg.eps_p, j, work, st);
+        launch_fr_regions(t, PR, j, n, d_thr, t_sw, d_fctr, st);
+        launch_fr_work(F, nF, PR, work, st);
+        launch_scan64(work, nF, ws->r_part.as<long long>(), wp, st);
+        launch_scan64(PR.rsize, NP, ws->r_part.as<long long>(), PR.roff, st);
+        launches += 9;
+        PS_CUDA(cudaMemcpyAsync(h_ll, wp + nF, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(h_ll + 1, PR.roff + NP, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(h_ll + 2, d_fctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        const long long E = h_ll[0], T = h_ll[1];
+        switched += h_ll[2];
+        const long long next_cap = std::max<long long>(1, h_ll[3]);  // distinct next entries <= sum of min(deg, n)
+        ws->stats.edge_gathers += E;
+        ws->stats.levels += 1;
+        if (E == 0) break;  // nothing left to push: every remaining probe ended, switched or was pruned
+        const int nx = cur ^ 1;
+        if ((size_t)next_cap * 16 > g->budget && B > 1) {  // a smaller batch may fit; one query just tries
+            *too_big = true;
+            return fail(PROBESIM_E_NOMEM, "frontier of one level exceeds the workspace budget");
+        }
+        PS_CUDA(ws->f_lp[nx].ensure(sizeof(int32_t) * next_cap));
+        PS_CUDA(ws->f_lx[nx].ensure(sizeof(int32_t) * next_cap));
+        PS_CUDA(ws->f_lv[nx].ensure(sizeof(long long) * next_cap));
+        const FrontierList Fn = list_of(nx);
+        // passes over probe ranges whose regions fit pass_slots
+        std::vector<int32_t> cuts{0};
+        if (T > pass_slots) {
+            std::vector<long long> roff(NP + 1);
+            PS_CUDA(cudaMemcpyAsync(roff.data(), PR.roff, sizeof(long long) * (NP + 1), cudaMemcpyDeviceToHost, st));
+            PS_CUDA(cudaStreamSynchronize(st));
+            int32_t p0 = 0;
+            while (p0 < NP) {
+                int32_t p1 = (int32_t)(std::upper_bound(roff.begin() + p0 + 1, roff.end(), roff[p0] + pass_slots) -
+                                       roff.begin()) - 1;
+                if (p1 <= p0) p1 = p0 + 1;
+                cuts.push_back(p1);
+                p0 = p1;
+            }
+        } else {
+            cuts.push_back(NP);
+        }
+        const int32_t npass = (int32_t)cuts.size() - 1;
+        ws->stats.table_passes += npass;
+        ws->stats.max_table_slots = std::max<int64_t>(ws->stats.max_table_slots, T);
+        std::vector<long long> fb(2 * (size_t)(npass + 1));  // per cut: first entry, work prefix there
+        if (npass == 1) {
+            fb[0] = 0; fb[1] = 0; fb[2] = nF; fb[3] = E;
+        } else {
+            PS_CUDA(ws->f_cuts.ensure(sizeof(int32_t) * cuts.size() + sizeof(long long) * 2 * cuts.size()));
+            int32_t *d_cuts = ws->f_cuts.as<int32_t>();
+            long long *d_fb = reinterpret_cast<long long *>(ws->f_cuts.as<char>() + ((sizeof(int32_t) * cuts.size() + 7) / 8 * 8));
+            PS_CUDA(cudaMemcpyAsync(d_cuts, cuts.data(), sizeof(int32_t) * cuts.size(), cudaMemcpyHostToDevice, st));
+            launch_fr_bounds(F.p, nF, wp, d_cuts, (int32_t)cuts.size(), d_fb, st);
+            ++launches;
+            PS_CUDA(cudaMemcpyAsync(fb.data(), d_fb, sizeof(long long) * fb.size(), cudaMemcpyDeviceToHost, st));
+            PS_CUDA(cudaStreamSynchronize(st));
+        }
+        const long long tslots = std::min<long long>(T, pass_slots + n);
+        PS_CUDA(ws->f_keys.ensure(sizeof(int32_t) * std::max<long long>(1, tslots)));
+        PS_CUDA(ws->f_vals.ensure(sizeof(unsigned long long) * std::max<long long>(1, tslots)));
+        PS_CUDA(ws->f_bcnt.ensure(sizeof(long long) * (fr_compact_blocks(tslots) + 1)));
+        PS_CUDA(ws->f_bpre.ensure(sizeof(long long) * (fr_compact_blocks(tslots) + 1)));
+        PS_CUDA(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(
+                                      std::max<int64_t>(nF, NP), fr_compact_blocks(tslots)))));
+        std::vector<long long> roff_cut(npass + 1, 0);
+        if (npass > 1) {  // region offsets at the cuts
+            for (int32_t c = 0; c <= npass; ++c)
+                PS_CUDA(cudaMemcpyAsync(&roff_cut[c], PR.roff + cuts[c], sizeof(long long), cudaMemcpyDeviceToHost, st));
+            PS_CUDA(cudaStreamSynchronize(st));
+        } else {
+            roff_cut[1] = T;
+        }
+        long long out_n = 0;
+        for (int32_t c = 0; c < npass; ++c) {
+            const long long r0 = roff_cut[c], Tc = roff_cut[c + 1] - r0;
+            FrontierExpand a;
+            a.wp = wp;
+            a.f_lo = fb[2 * c];
+            a.f_hi = fb[2 * (c + 1)];
+            a.e_lo = fb[2 * c + 1];
+            a.e_hi = fb[2 * (c + 1) + 1];
+            a.j = j;
+            a.keys = ws->f_keys.as<int32_t>();
+            a.vals = ws->f_vals.as<unsigned long long>();
+            a.rbase = r0;
+            a.acc = ws->f_acc.as<unsigned long long>();
+            a.n = n;
+            if (Tc > 0) {
+                PS_CUDA(cudaMemsetAsync(a.keys, 0xFF, sizeof(int32_t) * Tc, st));
+                PS_CUDA(cudaMemsetAsync(a.vals, 0, sizeof(unsigned long long) * Tc, st));
+            }
+            launch_fr_expand(dg, t, PR, F, a, st);
+            ++launches;
+            if (Tc > 0) {
+                const int64_t nb = fr_compact_blocks(Tc);
+                launch_fr_count(a.keys, Tc, ws->f_bcnt.as<long long>(), st);
+                launch_scan64(ws->f_bcnt.as<long long>(), nb, ws->r_part.as<long long>(), ws->f_bpre.as<long long>(), st);
+                launch_fr_write(a.keys, a.vals, Tc, PR.roff, cuts[c], cuts[c + 1], r0, ws->f_bpre.as<long long>(), Fn,
+                                out_n, next_cap, st);
+                launches += 5;
+                PS_CUDA(cudaMemcpyAsync(h_ll, ws->f_bpre.as<long long>() + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
+                PS_CUDA(cudaStreamSynchronize(st));
+                out_n += h_ll[0];
+                if (out_n > next_cap) return fail(PROBESIM_E_CUDA, "internal: frontier larger than its bound");
+            }
+        }
+        launch_fr_advance(t, PR, st);
+        ++launches;
+        nF = out_n;
+        cur = nx;
+    }
+    ws->stats.switched += switched;
+    // Sec. 4.4: Alg. 3 for every walk through a switched tree node
+    const int32_t *counts = nullptr;
+    if (switched > 0) {
+        PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, t.walk_slot, t_sw, launches, st));
+        counts = ws->r_counts.as<int32_t>();
+    }
+    launch_fr_finalize(n, B, qb.node, ws->f_acc.as<unsigned long long>(), counts, qb.inv_nr, dg.ext2int, d_out, st);
     ++launches;
     PS_CUDA(cudaGetLastError());
     PS_CUDA(cudaStreamSynchronize(st));
@@ -902,9 +1180,14 @@ static probesim_status run_queries(probesim_graph *g, Workspace *ws, const probe
     while (done < nq) {
         const int32_t B = std::min(chunk, nq - done);
         bool too_big = false;
-        probesim_status s = g->cfg.probe_mode == PROBESIM_PROBE_RANDOMIZED
-                                ? run_batch_rand(g, ws, q + done, B, d_out + (int64_t)done * g->dg.n, st, &too_big)
-                                : run_batch(g, ws, q + done, B, d_out + (int64_t)done * g->dg.n, st, &too_big);
+        float *out = d_out + (int64_t)done * g->dg.n;
+        probesim_status s;
+        if (g->cfg.probe_mode == PROBESIM_PROBE_RANDOMIZED)
+            s = run_batch_rand(g, ws, q + done, B, out, st, &too_big);
+        else if (g->cfg.probe_mode == PROBESIM_PROBE_SWITCH || g->cfg.eps_p > 0.f)
+            s = run_batch_frontier(g, ws, q + done, B, out, st, &too_big);
+        else
+            s = run_batch(g, ws, q + done, B, out, st, &too_big);
         if (s == PROBESIM_OK) {
             done += B;
             continue;
@@ -965,8 +1248,6 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
     if (c.l_max < 1 || c.l_max > 255) return fail(PROBESIM_E_INVALID, "l_max must lie in [1, 255]");
     if (!(c.eps_p >= 0.f) || !(c.c0 >= 0.f)) return fail(PROBESIM_E_INVALID, "eps_p and c0 must be >= 0");
     if (c.probe_mode < 0 || c.probe_mode > 2) return fail(PROBESIM_E_INVALID, "unknown probe_mode");
-    if (c.probe_mode == PROBESIM_PROBE_SWITCH || c.eps_p != 0.f)
-        return fail(PROBESIM_E_UNSUPPORTED, "this build runs the deterministic and randomized PROBE without Pruning Rule 2");
     std::vector<int32_t> hs, hd;
     PS_TRY(fetch_ids(src, m, hs));
     PS_TRY(fetch_ids(dst, m, hd));
@@ -980,7 +1261,8 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
     cudaGetDevice(&g->device);
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    g->budget = (size_t)(0.6 * (double)tot);
+    g->budget0 = (size_t)(0.6 * (double)tot);
+    g->budget = g->budget0;
     if (g->ws0.pin_s.ensure(65536) != cudaSuccess) {
         delete g;
         return fail(PROBESIM_E_NOMEM, "pinned host allocation failed");
@@ -997,6 +1279,14 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
     }
     std::vector<uint64_t>().swap(g->keys);  // later updates merge on the device
     *out = g;
+    return PROBESIM_OK;
+}
+
+probesim_status probesim_set_memory_budget(probesim_graph *g, double bytes) {
+    if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
+    if (!(bytes >= 0.0)) return fail(PROBESIM_E_INVALID, "bytes must be >= 0");
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->budget = bytes > 0.0 ? (size_t)bytes : g->budget0;
     return PROBESIM_OK;
 }
 

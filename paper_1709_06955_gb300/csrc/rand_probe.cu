@@ -125,10 +125,19 @@ __device__ __forceinline__ int32_t walk_query(const int32_t *walk_base, int32_t 
     return lo;
 }
 
-// per walk: number of probes (len - 1)
-__global__ void k_inst_count(const int32_t *__restrict__ lens, int32_t W, long long *cnt) {
+// instance (w, i) runs unless a filter is given and the tree slot of its prefix is not flagged
+__device__ __forceinline__ bool inst_on(const int32_t *walk_slot, const uint8_t *t_sw, int32_t l_max, int32_t w, int32_t i) {
+    return !walk_slot || t_sw[walk_slot[(int64_t)w * l_max + i - 1]];
+}
+
+// per walk: number of probes (len - 1, or the flagged ones)
+__global__ void k_inst_count(const int32_t *__restrict__ lens, int32_t W, long long *cnt,
+                             const int32_t *__restrict__ walk_slot, const uint8_t *__restrict__ t_sw, int32_t l_max) {
     const int32_t w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w < W) cnt[w] = lens[w] > 1 ? lens[w] - 1 : 0;
+    if (w >= W) return;
+    long long c = 0;
+    for (int32_t i = 2; i <= lens[w]; ++i) c += inst_on(walk_slot, t_sw, l_max, w, i);
+    cnt[w] = c;
 }
 
 // instance (walk w, prefix length i) for i = 2..len; its level-0 frontier {u_i} goes into the table and list
@@ -169,15 +178,16 @@ __global__ void k_inst_init(QueryBatch q, const int64_t *__restrict__ out_off, c
                             int32_t W, int32_t l_max, const int32_t *__restrict__ walks,
                             const long long *__restrict__ inst_off, int32_t *inst_walk, int32_t *inst_len,
                             int32_t *inst_q, uint32_t *inst_k, int32_t *fr_inst, int32_t *fr_node,
-                            unsigned long long *fr_count, unsigned long long *keys, int64_t cap, int32_t *overflow) {
+                            unsigned long long *fr_count, unsigned long long *keys, int64_t cap, int32_t *overflow,
+                            const int32_t *__restrict__ walk_slot, const uint8_t *__restrict__ t_sw) {
     const int32_t w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= W) return;
     const int32_t len = lens[w];
-    const int64_t base = inst_off[w];
+    int64_t id = inst_off[w];
     const int32_t b = walk_query(q.walk_base, q.B, w);
     const uint32_t k = (uint32_t)(q.walk_k0[b] + (w - q.walk_base[b]));
     for (int32_t i = 2; i <= len; ++i) {
-        const int64_t id = base + (i - 2);
+        if (!inst_on(walk_slot, t_sw, l_max, w, i)) continue;
         inst_walk[id] = w;
         inst_len[id] = i;
         inst_q[id] = b;
@@ -189,6 +199,7 @@ __global__ void k_inst_init(QueryBatch q, const int64_t *__restrict__ out_off, c
             fr_inst[pos] = (int32_t)id;
             fr_node[pos] = u;
         }
+        ++id;
     }
 }
 
@@ -296,17 +307,19 @@ __global__ void k_rand_finalize(int32_t n, int32_t B, const int32_t *__restrict_
     out[(int64_t)b * n + v] = s;
 }
 
-void launch_inst_count(const int32_t *lens, int32_t W, long long *cnt, cudaStream_t s) {
-    if (W > 0) k_inst_count<<<(W + 255) / 256, 256, 0, s>>>(lens, W, cnt);
+void launch_inst_count(const int32_t *lens, int32_t W, long long *cnt, const int32_t *walk_slot, const uint8_t *t_sw,
+                       int32_t l_max, cudaStream_t s) {
+    if (W > 0) k_inst_count<<<(W + 255) / 256, 256, 0, s>>>(lens, W, cnt, walk_slot, t_sw, l_max);
 }
 void launch_inst_init(const QueryBatch &q, const DeviceGraph &g, const int32_t *lens, int32_t W, int32_t l_max,
                       const int32_t *walks, const long long *inst_off, int32_t *inst_walk, int32_t *inst_len,
                       int32_t *inst_q, uint32_t *inst_k, int32_t *fr_inst, int32_t *fr_node,
                       unsigned long long *fr_count, unsigned long long *keys, int64_t cap, int32_t *overflow,
-                      cudaStream_t s) {
+                      const int32_t *walk_slot, const uint8_t *t_sw, cudaStream_t s) {
     if (W > 0)
         k_inst_init<<<(W + 255) / 256, 256, 0, s>>>(q, g.out_off, lens, W, l_max, walks, inst_off, inst_walk, inst_len,
-                                                    inst_q, inst_k, fr_inst, fr_node, fr_count, keys, cap, overflow);
+                                                    inst_q, inst_k, fr_inst, fr_node, fr_count, keys, cap, overflow,
+                                                    walk_slot, t_sw);
 }
 void launch_frontier_degree(const int32_t *fr_inst, const int32_t *fr_node, int64_t F, const int32_t *inst_len, int32_t j,
                             const int64_t *out_off, long long *deg, cudaStream_t s) {

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(256) k_trie_insert(QueryBatch q, int32_t W, in
         const int32_t u = row[i - 1];
         const int64_t s = table_insert(t.key, t.cap, ((unsigned long long)(uint32_t)p << 32) | (uint32_t)u);
         if (s < 0) { atomicExch(&ctr->overflow, 1); return; }
+        if (t.walk_slot) t.walk_slot[(int64_t)wid * l_max + i - 1] = (int32_t)s;
         t.node[s] = u;
         t.parent[s] = (int32_t)p;
         t.depth[s] = i;

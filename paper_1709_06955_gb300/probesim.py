@@ -22,6 +22,7 @@ EXPORTS = [
     "probesim_last_error", "probesim_topk_select_noalloc", "probesim_server_config_default",
     "probesim_server_create", "probesim_server_submit", "probesim_server_update", "probesim_server_poll",
     "probesim_server_get_stats", "probesim_server_destroy", "probesim_autotune", "probesim_get_tuning",
+    "probesim_set_memory_budget",
 ]
 
 
@@ -39,7 +40,8 @@ class Stats(C.Structure):
     _fields_ = [("walks", C.c_int64), ("walk_nodes", C.c_int64), ("tree_nodes", C.c_int64), ("vectors", C.c_int64),
                 ("levels", C.c_int64), ("edge_gathers", C.c_int64), ("probe_launches", C.c_int64),
                 ("probe_ms", C.c_double), ("probe_bytes", C.c_double), ("kernel_launches", C.c_int64),
-                ("phase_ms", C.c_double * 12), ("max_columns", C.c_int64)]
+                ("phase_ms", C.c_double * 12), ("max_columns", C.c_int64), ("probes", C.c_int64),
+                ("switched", C.c_int64), ("table_passes", C.c_int64), ("max_table_slots", C.c_int64)]
 
     PHASES = ["walks", "tree", "accumulate", "scatter", "zero_rows", "pull", "push", "gamma", "estimates",
               "host_schedule"]
@@ -102,6 +104,7 @@ def load(path=None):
     L.probesim_single_source.argtypes = [vp, P(Query), C.c_int32, vp, vp]
     L.probesim_topk.argtypes = [vp, P(Query), C.c_int32, C.c_int32, vp, vp, vp]
     L.probesim_set_profiling.argtypes = [vp, C.c_int32]
+    L.probesim_set_memory_budget.argtypes = [vp, C.c_double]
     L.probesim_get_stats.argtypes = [vp, P(Stats)]
     L.probesim_topk_select_noalloc.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp, vp]
     L.probesim_server_config_default.argtypes = [P(ServerConfig)]
@@ -299,6 +302,10 @@ class Graph:
         bps = (C.c_int32 * 6)()
         _check(load().probesim_get_tuning(self._h, C.byref(wide), bps))
         return {"wide_tile": wide.value, "blocks_per_sm": {1 << i: bps[i] for i in range(6)}}
+
+    def set_memory_budget(self, nbytes):
+        """Device memory one call's working buffers may take (0 = the default, 60% of the device)."""
+        _check(load().probesim_set_memory_budget(self._h, float(nbytes)))
 
     def set_profiling(self, on=True):
         _check(load().probesim_set_profiling(self._h, 1 if on else 0))
