@@ -1,19 +1,28 @@
 #!/usr/bin/env python
 """Benchmark: single-source SimRank queries/s at eps = 0.1 on a synthetic R-MAT graph.
 
-Workload (one GPU): R-MAT (a,b,c,d) = (.57,.19,.19,.05), n = 2^20, m = 2^24 distinct edges, seeded; query
-nodes drawn uniformly from the nodes with in-degree >= 1; c = 0.6, eps = 0.1, delta = 0.01 (n_r = 3,325),
-deterministic PROBE, FP32 scores.  A step is one single-source query through the C ABI (walks, tree,
-level loop, estimates), queries run one at a time; L2 is flushed between steps (outside the timed events).
-Also reported: the same queries in batches, the end-to-end number with host buffers, p50/p99 latency,
-the PROBE level kernel's achieved bandwidth against the measured HBM copy peak, and the CPU oracle on a
-bounded sample of the same workload.  The timed steps run with profiling off; per-phase times and the
-pull's own duration come from a second, profiled pass over the first (up to ten) queries, in which the
-level loop runs on one stream.
+Headline workload (one GPU): R-MAT (a,b,c,d) = (.57,.19,.19,.05), n = 2^20, m = 2^24 distinct edges, seeded;
+query nodes drawn uniformly from the nodes with in-degree >= 1; c = 0.6, eps = 0.1, delta = 0.01
+(n_r = 3,325), deterministic PROBE, FP32 scores.  A step is one single-source query through the C ABI
+(walks, tree, level loop, estimates), queries run one at a time; L2 is flushed between steps (outside the
+timed events).  Also reported, each on its own line of the JSON object:
+  batched      the same queries in calls of 2, 4 and 8, against the same queries one at a time
+  switch       the Sec. 4.4 switch (c0 = 0.01) on the same graph, one at a time and in calls of 8
+  mixed_eps_topk  R-MAT 2^22 (m = 2^26): 256 queries in one top-50 call, eps 0.1 / 0.05 alternating
+               (n_r 3,574 / 14,296), switch mode
+  serving      Poisson arrivals into the continuous-batching server at rates bracketing its capacity, top-k
+               with k uniform over {10, 50, 100}, one window with edge-update batches every 100 ms
+  serving_2p23 R-MAT 2^23 (m = 2^27), eps uniform over {0.1, 0.05, 0.025}, switch mode, update batches of
+               10k edges every 100 ms, Poisson rates bracketing capacity
+  e2e          the headline with host output buffers (the scores copied back inside the timed region)
+  roofline     the PROBE level kernel's achieved bandwidth against the measured HBM copy peak
+  cpu_baseline the FP64 oracle on every host core, on a bounded sample of the headline workload
+The timed steps run with profiling off; per-phase times and the pull's own duration come from a second,
+profiled pass over the first (up to ten) queries, in which the level loop runs on one stream.
 
 ``--impl reference`` times the CPU oracle (the reference implementation of this build) on the same
-workload and metric.  Multi-GPU runs (torchrun) are replicas: each rank owns a copy of the graph and its
-own share of queries, with no collective on the data path.
+workload and metric, on every host core.  Multi-GPU runs (torchrun) are replicas: each rank owns a copy of the
+graph and its own share of queries, with no collective on the data path.
 """
 import argparse
 import csv
@@ -41,19 +50,24 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=8, help="queries per call in the batched leg")
+    ap.add_argument("--batches", default="2,4,8", help="queries per call in the batched legs")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--cpu-walks-per-core", type=int, default=2, help="CPU-baseline sample size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-rates", default="12,60", help="Poisson arrival rates of the serving leg (q/s), comma-separated")
+    ap.add_argument("--serve-rates", default="10,20,30,35,40,50",
+                    help="Poisson arrival rates of the serving sweep on the headline graph (q/s)")
+    ap.add_argument("--serve-update-rate", type=float, default=20.0,
+                    help="rate of the serving window with edge-update batches (0 = none)")
     ap.add_argument("--serve-updates", type=int, default=10000, help="edges per update batch, one batch per 100 ms")
-    ap.add_argument("--serve-plain-rate", type=float, default=60.0,
-                    help="an extra serving window at this rate without updates (0 = none)")
     ap.add_argument("--serve-workers", type=int, default=3, help="server workers (concurrent batch pipelines)")
     ap.add_argument("--serve-max-batch", type=int, default=2, help="largest batch a server worker takes")
-    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the serving leg")
-    ap.add_argument("--mixed-batch", type=int, default=0,
-                    help="queries of the optional mixed-eps top-k leg (eps 0.1 / 0.05 alternating, k = 50); 0 = off")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of each serving rate")
+    ap.add_argument("--switch-c0", type=float, default=0.01, help="c0 of the switch legs (Sec. 4.4)")
+    ap.add_argument("--mixed-batch", type=int, default=256,
+                    help="queries of the mixed-eps top-50 call on R-MAT 2^22 (0 = off)")
+    ap.add_argument("--serve23-rates", default="2,4,6,8",
+                    help="arrival rates of the serving leg on R-MAT 2^23 (empty = off)")
+    ap.add_argument("--serve23-seconds", type=float, default=5.0)
     return ap.parse_args()
 
 
@@ -164,35 +178,63 @@ def load_workload(name):
     return n, s, d, qs
 
 
-def cpu_baseline(n, s, d, qs, budget_s):
-    """The oracle (Alg. 1, FP64, one thread) on walks 0, 1, 2, ... of query 0 until budget_s has passed;
-    queries/s extrapolated from the time per walk."""
+def oracle_sample_rate(O, qs, nr, walks, budget_s=None, threads=None):
+    """The oracle (Alg. 1, FP64) on a bounded sample of a workload, on every host core: the samples are walks
+    0..walks-1 of each query in ``qs`` (a walk k of query u is Alg. 1 restricted to walk k, weighted 1/n_r), run
+    by one thread per core (the C oracle releases the GIL, so the threads run in parallel); with ``budget_s``, no
+    walk starts after the budget.  Returns (queries/s = walks/s / n_r, walks done, seconds, threads)."""
+    import concurrent.futures
+    threads = threads or len(os.sched_getaffinity(0))
+    items = [(t, k) for k in range(walks) for t in range(len(qs))]
+    lock = threading.Lock()
+    it = iter(items)
+    done = [0]
+    t0 = time.perf_counter()
+
+    def work():
+        while True:
+            with lock:
+                if budget_s is not None and time.perf_counter() - t0 >= budget_s:
+                    return
+                nxt = next(it, None)
+            if nxt is None:
+                return
+            t, k = nxt
+            O.single_source(int(qs[t]), eps=EPS, seed=3, qid=t, walk_begin=k, walk_end=k + 1)
+            with lock:
+                done[0] += 1
+
+    with concurrent.futures.ThreadPoolExecutor(threads) as ex:
+        for f in [ex.submit(work) for _ in range(threads)]:
+            f.result()
+    el = time.perf_counter() - t0
+    return done[0] / el / nr, done[0], el, threads
+
+
+def cpu_baseline(n, s, d, qs, walks_per_core):
+    """The oracle on every host core over a fixed sample of the headline workload: walks 0..K-1 of 4 queries,
+    K = walks_per_core * cores / 4, every walk run to the end (no time cut-off, which would keep the short walks
+    and bias the rate); queries/s extrapolated from walks/s and n_r."""
     from oracle import build as obuild, core
     obuild.build()
     O = core.Graph(n, s, d)
     nr = core.num_walks(0.6, EPS, 0.01, n)
-    u = int(qs[0])
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        O.single_source(u, eps=EPS, seed=3, qid=0, walk_begin=k, walk_end=k + 1)
-        k += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or k >= 256:
-            break
-    per_walk = el / k
-    return {"value": 1.0 / (per_walk * nr), "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": "walks 0..%d of 1 query (of n_r=%d) on %s, Alg. 1 FP64 single-threaded, %.1f s; "
-                      "queries/s extrapolated from the time per walk" % (k - 1, nr, "%d-node graph" % n, el)}
+    th = len(os.sched_getaffinity(0))
+    K = max(1, (walks_per_core * th + 3) // 4)
+    rate, k, el, th = oracle_sample_rate(O, qs[:4], nr, K, threads=th)
+    return {"value": rate, "unit": "queries/s", "cores": th, "kind": "oracle",
+            "sample": "walks 0..%d of 4 queries (%d walks, n_r=%d each) on the %d-node graph, Alg. 1 FP64, one "
+                      "thread per host core, %.1f s; queries/s = walks/s / n_r (extrapolated)" % (K - 1, k, nr, n, el)}
 
 
-def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, rank, workers=3, max_batch=2):
+def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, rank, workers=3, max_batch=2,
+                eps_choices=(EPS,), seed_base=4, qid_base=900000):
     """For each arrival rate: queries arrive as a Poisson process for `seconds` into a fresh continuous-batching
-    server (top-k, k uniform over {10, 50, 100}), while every 100 ms an update batch of updates_per_tick edges
-    (half random inserts, half deletes of edges of the original graph) enters the same FIFO.  Returns one
-    record per rate: throughput, p50/p99 latency, mean batch size, updates applied."""
+    server (top-k, k uniform over {10, 50, 100}, eps uniform over eps_choices), while every 100 ms an update
+    batch of updates_per_tick edges (half random inserts, half deletes of edges of the original graph) enters
+    the same FIFO.  Returns one record per rate: throughput, p50/p99 latency, mean batch size, updates applied."""
     import numpy as np
-    rng = np.random.default_rng(4 + rank)
+    rng = np.random.default_rng(seed_base + rank)
     out = []
     for rate in rates:
         S = probesim.Server(G, workers=workers, max_batch=max_batch, kmax=100)
@@ -200,6 +242,7 @@ def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, 
         arrivals = np.cumsum(gaps)
         arrivals = arrivals[arrivals < seconds]
         ks = np.array([10, 50, 100])[rng.integers(0, 3, arrivals.size)]
+        es = np.array(eps_choices)[rng.integers(0, len(eps_choices), arrivals.size)]
         ticks = np.arange(0.0, seconds, 0.1) if updates_per_tick > 0 else np.zeros(0)
         events = sorted([(t, 0, i) for i, t in enumerate(arrivals)] + [(t, 1, j) for j, t in enumerate(ticks)])
         half = updates_per_tick // 2
@@ -210,7 +253,8 @@ def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, 
             if ta > now:
                 time.sleep(ta - now)
             if kind == 0:
-                S.submit(probesim.make_queries([qs[i % len(qs)]], eps=EPS, k=int(ks[i]), query_ids=[900000 + i]))
+                S.submit(probesim.make_queries([qs[i % len(qs)]], eps=float(es[i]), k=int(ks[i]),
+                                               query_ids=[qid_base + i]))
             else:
                 S.update(rng.integers(0, n, half), rng.integers(0, n, half), insert=True)
                 pick = rng.integers(0, src.size, half)
@@ -223,7 +267,7 @@ def serving_leg(probesim, G, n, src, dst, qs, rates, seconds, updates_per_tick, 
         out.append({"arrival_rate_qps": rate, "queries": int(arrivals.size), "qps": st["qps"], "p50_ms": st["p50_ms"],
                     "p99_ms": st["p99_ms"], "mean_batch": st["mean_batch"], "update_batches": st["updates_applied"],
                     "edges_per_update_tick": updates_per_tick, "workers": workers, "max_batch": max_batch,
-                    "k": "uniform {10, 50, 100}", "eps": EPS})
+                    "k": "uniform {10, 50, 100}", "eps": "uniform {%s}" % ", ".join("%g" % e for e in eps_choices)})
     return out
 
 
@@ -236,25 +280,37 @@ def run_reference(args):
     n, s, d, qs = load_workload(args.workload)
     O = core.Graph(n, s, d)
     nr = core.num_walks(0.6, EPS, 0.01, n)
-    # one step: one walk of one query through Alg. 1 (a bounded sample of the query)
-    for i in range(args.warmup):
-        O.single_source(int(qs[i % len(qs)]), eps=EPS, seed=3, qid=i, walk_begin=0, walk_end=1)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        q = i % len(qs)
-        O.single_source(int(qs[q]), eps=EPS, seed=3, qid=q, walk_begin=i // len(qs), walk_end=i // len(qs) + 1)
-    el = time.perf_counter() - t0
-    qps = args.steps / el / nr
-    line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
+    threads = len(os.sched_getaffinity(0))
+    # a step: one walk per host core (Alg. 1 restricted to that walk), walks taken in order over 4 queries
+    oracle_sample_rate(O, qs[:4], nr, max(1, (args.warmup * threads + 3) // 4), threads=threads)
+    walks = max(1, (args.steps * threads + 3) // 4)
+    rate, k, el, th = oracle_sample_rate(O, qs[:4], nr, walks, threads=threads)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": describe_workload(args.workload, n, len(s)),
-                       "step": "one walk of one query (Alg. 1 on it), queries/s = walks/s / n_r"},
-            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d walks over %d queries (of n_r=%d each)" % (args.steps, min(args.steps, len(qs)), nr)},
-            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                       "step": "one walk per host core (Alg. 1 on it), queries/s = walks/s / n_r"},
+            "cpu_baseline": {"value": rate, "unit": "queries/s", "cores": th, "kind": "oracle",
+                             "sample": "%d walks: walks 0..%d of 4 queries (n_r=%d each), one thread per core"
+                                       % (k, walks - 1, nr)},
+            "e2e": {"value": rate, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def timed_calls(G, calls, out, stream, flush):
+    """CUDA-event milliseconds of each call (L2 flushed before each, outside the events)."""
+    import torch
+    ms = []
+    for q in calls:
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.single_source(q, out=out, stream=stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
 
 
 def run_ours(args):
@@ -267,18 +323,23 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1709_06955_gb300 import build, probesim
+    from paper_1709_06955_gb300 import build, probesim, synth
     build.build()
     n, s, d, qs = load_workload(args.workload)
     G = probesim.Graph(n, s, d)
     tuning = G.autotune()  # launch shape of the pull kernel, chosen on this graph before timing
+    nr_headline = G.num_walks(EPS)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     nq = len(qs)
 
-    def query(i):
+    def query(i, **kw):
         j = replica_query_id(rank, i)
-        return probesim.make_queries([qs[j % nq]], eps=EPS, k=50, query_ids=[j])
+        return probesim.make_queries([qs[j % nq]], eps=kw.get("eps", EPS), k=50, query_ids=[j])
+
+    def qbatch(i0, B):
+        ids = [replica_query_id(rank, i0 + j) for j in range(B)]
+        return probesim.make_queries([qs[j % nq] for j in ids], eps=EPS, query_ids=ids)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
     out = torch.zeros((1, n), dtype=torch.float32, device=dev)
@@ -335,70 +396,44 @@ def run_ours(args):
     G.set_profiling(False)
     torch.cuda.synchronize(dev)
 
-    # batched leg: the same number of queries, args.batch per call
-    B = max(1, args.batch)
-    nb = max(1, args.steps // B)
-    outb = torch.zeros((B, n), dtype=torch.float32, device=dev)
-    Qb = [probesim.make_queries([qs[replica_query_id(rank, args.warmup + i * B + j) % nq] for j in range(B)],
-                                eps=EPS, query_ids=[replica_query_id(rank, args.warmup + i * B + j) for j in range(B)])
-          for i in range(nb)]
-    G.single_source(Qb[0], out=outb, stream=sptr)
-    bev = []
-    barrier()
-    for i in range(nb):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        G.single_source(Qb[i], out=outb, stream=sptr)
-        b.record(stream)
-        bev.append((a, b))
-    barrier()
-    bms = sum(a.elapsed_time(b) for a, b in bev)
-    batched_qps = nb * B / (bms / 1e3)
-    # the batches hold the first nb * B queries of the timed leg: the same queries one at a time
-    single_same_qps = nb * B / (sum(lat[:nb * B]) / 1e3)
+    # batched legs: the timed leg's queries again, B per call, against the same queries one at a time
+    batched = []
+    for B in [int(x) for x in args.batches.split(",") if x]:
+        nb = max(1, args.steps // B)
+        outb = torch.zeros((B, n), dtype=torch.float32, device=dev)
+        calls = [qbatch(args.warmup + i * B, B) for i in range(nb)]
+        G.single_source(calls[0], out=outb, stream=sptr)
+        barrier()
+        bms = sum(timed_calls(G, calls, outb, stream, flush))
+        barrier()
+        batched.append({"batch": B, "value": nb * B / (bms / 1e3), "unit": "queries/s", "calls": nb,
+                        "queries": nb * B, "same_queries_one_at_a_time": nb * B / (sum(lat[:nb * B]) / 1e3)})
+        del outb
+    best = max(batched, key=lambda r: r["value"]) if batched else None
 
-    # optional mixed-eps top-k leg (the batched configuration's pattern): one call of --mixed-batch queries,
-    # eps alternating 0.1 / 0.05 (uneven n_r), top-50 per query; the library cuts the call into batches that
-    # fit its workspace budget
-    mixed = None
-    if args.mixed_batch > 0:
-        MB = args.mixed_batch
-        eps_mix = [EPS if j % 2 == 0 else EPS / 2 for j in range(MB)]
-        Qm = probesim.make_queries([qs[replica_query_id(rank, 5000 + j) % nq] for j in range(MB)], eps=eps_mix, k=50,
-                                   query_ids=[replica_query_id(rank, 5000 + j) for j in range(MB)])
-        mids = torch.empty((MB, 50), dtype=torch.int32, device=dev)
-        mvals = torch.empty((MB, 50), dtype=torch.float32, device=dev)
-        barrier()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        G.topk(Qm, kmax=50, ids=mids, vals=mvals, stream=sptr)
-        b.record(stream)
-        barrier()
-        mms = a.elapsed_time(b)
-        mixed = {"queries": MB, "eps": "%g / %g alternating" % (EPS, EPS / 2), "k": 50, "value": MB / (mms / 1e3),
-                 "unit": "queries/s", "ms": mms,
-                 "n_r": [int(G.num_walks(EPS)), int(G.num_walks(EPS / 2))]}
+    # the switch of Sec. 4.4 on the same graph: a few queries one at a time and in calls of 8
+    GS = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_SWITCH, c0=args.switch_c0)
+    GS.single_source(query(0), out=out, stream=sptr)
+    sq = min(args.steps, 40)
+    sw_ms = timed_calls(GS, [query(args.warmup + i) for i in range(sq)], out, stream, flush)
+    sst = GS.stats()
+    out8 = torch.zeros((8, n), dtype=torch.float32, device=dev)
+    sw8_ms = timed_calls(GS, [qbatch(args.warmup + 8 * i, 8) for i in range(sq // 8)], out8, stream, flush)
+    switch = {"c0": args.switch_c0, "eps": EPS, "value": sq / (sum(sw_ms) / 1e3), "unit": "queries/s", "queries": sq,
+              "batched8_value": 8 * (sq // 8) / (sum(sw8_ms) / 1e3),
+              "last_query": {k: sst[k] for k in ("probes", "switched", "edge_gathers", "levels", "max_table_slots")}}
+    GS.close()
+    del out8
 
     # randomized PROBE (Alg. 3) on the same graph: a few queries one at a time
     GR = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_RANDOMIZED)
     rq = 10
     GR.single_source(query(0), out=out, stream=sptr)
-    rsum = {"edge_gathers": 0, "levels": 0, "walk_nodes": 0}
-    rand_s = 0.0
-    for i in range(rq):
-        barrier()
-        r0 = time.perf_counter()
-        GR.single_source(query(args.warmup + i), out=out, stream=sptr)
-        barrier()
-        rand_s += time.perf_counter() - r0
-        rst = GR.stats()  # describes the last call
-        for k in rsum:
-            rsum[k] += rst[k]
+    rand_ms = timed_calls(GR, [query(args.warmup + i) for i in range(rq)], out, stream, flush)
+    rst = GR.stats()
     GR.close()
-    randomized = {"value": rq / rand_s, "unit": "queries/s", "queries": rq,
-                  "candidates_per_query": rsum["edge_gathers"] / rq, "levels_per_query": rsum["levels"] / rq,
-                  "walk_nodes_per_query": rsum["walk_nodes"] / rq}
+    randomized = {"value": rq / (sum(rand_ms) / 1e3), "unit": "queries/s", "queries": rq,
+                  "candidates_last_query": rst["edge_gathers"], "levels_last_query": rst["levels"]}
 
     # end-to-end through the C ABI with host buffers: query struct in, pinned host scores out
     host_out = torch.empty((1, n), dtype=torch.float32, pin_memory=True)
@@ -413,14 +448,68 @@ def run_ours(args):
     e2e_s = time.perf_counter() - e0
     e2e_qps = e2e_steps / e2e_s
 
-    # serving leg (last: its update batches change the graph): Poisson arrivals into the continuous-batching
-    # server at each rate, with edge-update batches every 100 ms
+    # serving sweep on the headline graph (last for this graph: the update window changes it)
     rates = [float(r) for r in args.serve_rates.split(",") if r]
-    serving = serving_leg(probesim, G, n, s, d, qs, rates, args.serve_seconds, args.serve_updates, rank,
-                          args.serve_workers, args.serve_max_batch)
-    if args.serve_plain_rate > 0:  # the same at a saturating rate without updates: comparable to one per call
-        serving += serving_leg(probesim, G, n, s, d, qs, [args.serve_plain_rate], args.serve_seconds, 0, rank,
-                               args.serve_workers, args.serve_max_batch)
+    serving = serving_leg(probesim, G, n, s, d, qs, rates, args.serve_seconds, 0, rank, args.serve_workers,
+                          args.serve_max_batch)
+    if args.serve_update_rate > 0:
+        serving += serving_leg(probesim, G, n, s, d, qs, [args.serve_update_rate], args.serve_seconds,
+                               args.serve_updates, rank, args.serve_workers, args.serve_max_batch)
+    G.close()
+    torch.cuda.synchronize(dev)
+
+    # R-MAT 2^22: 256 queries in one top-50 call, eps alternating 0.1 / 0.05 (uneven n_r), switch mode
+    mixed = None
+    if args.mixed_batch > 0:
+        n22, s22, d22 = synth.rmat_device(22, 16 << 22, seed=1, device=dev)
+        torch.cuda.empty_cache()  # the generator's scratch goes back to the device before the library allocates
+        q22 = synth.queries(n22, d22, args.mixed_batch, seed=2)
+        t0 = time.perf_counter()
+        G22 = probesim.Graph(n22, s22, d22, probe_mode=probesim.PROBE_SWITCH, c0=args.switch_c0)
+        create_s = time.perf_counter() - t0
+        MB = args.mixed_batch
+        eps_mix = [EPS if j % 2 == 0 else EPS / 2 for j in range(MB)]
+        mids = torch.empty((MB, 50), dtype=torch.int32, device=dev)
+        mvals = torch.empty((MB, 50), dtype=torch.float32, device=dev)
+        G22.topk(probesim.make_queries(q22[:8], eps=EPS, k=50, query_ids=np.arange(8) + 70000), kmax=50,
+                 ids=mids[:8], vals=mvals[:8], stream=sptr)  # warm-up
+        Qm = probesim.make_queries(q22, eps=eps_mix, k=50, query_ids=[replica_query_id(rank, 5000 + j) for j in range(MB)])
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G22.topk(Qm, kmax=50, ids=mids, vals=mvals, stream=sptr)
+        b.record(stream)
+        barrier()
+        mms = a.elapsed_time(b)
+        mst = G22.stats()
+        mixed = {"graph": "R-MAT (.57,.19,.19,.05) n=2^22 m=%d (drawn on the GPU), seed 1" % int(s22.numel()),
+                 "queries": MB, "calls": 1, "eps": "%g / %g alternating" % (EPS, EPS / 2), "k": 50,
+                 "probe": "switch (Sec. 4.4), c0=%g" % args.switch_c0, "value": MB / (mms / 1e3),
+                 "unit": "queries/s", "ms": mms, "graph_create_s": create_s,
+                 "n_r": [int(G22.num_walks(EPS)), int(G22.num_walks(EPS / 2))],
+                 "probes": mst["probes"], "switched": mst["switched"], "det_edge_pushes": mst["edge_gathers"]}
+        G22.close()
+        del n22, s22, d22, mids, mvals
+        torch.cuda.empty_cache()
+
+    # serving on R-MAT 2^23: eps uniform over {0.1, 0.05, 0.025}, k over {10, 50, 100}, switch mode, 10k-edge
+    # update batches every 100 ms
+    serving23 = None
+    r23 = [float(r) for r in args.serve23_rates.split(",") if r]
+    if r23:
+        n23, s23, d23 = synth.rmat_device(23, 16 << 23, seed=1, device=dev)
+        torch.cuda.empty_cache()
+        q23 = synth.queries(n23, d23, 1000, seed=2)
+        G23 = probesim.Graph(n23, s23, d23, probe_mode=probesim.PROBE_SWITCH, c0=args.switch_c0)
+        s23h, d23h = s23.cpu().numpy(), d23.cpu().numpy()
+        del s23, d23
+        G23.single_source(probesim.make_queries(q23[:1], eps=EPS, query_ids=[1]), out=torch.zeros((1, n23), device=dev))
+        serving23 = serving_leg(probesim, G23, n23, s23h, d23h, q23, r23, args.serve23_seconds, args.serve_updates,
+                                rank, args.serve_workers, args.serve_max_batch, eps_choices=(0.1, 0.05, 0.025),
+                                seed_base=40, qid_base=800000)
+        G23.close()
+        del s23h, d23h
+        torch.cuda.empty_cache()
 
     if rank != 0:
         if world > 1:
@@ -449,26 +538,27 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": describe_workload(args.workload, n, len(s)) +
-                                   " (n_r=%d), deterministic PROBE, one query per call" % G.num_walks(EPS),
+                                   " (n_r=%d), deterministic PROBE, one query per call" % nr_headline,
                        "queries": "uniform over nodes with in-degree >= 1", "l2": "flushed between steps (256 MB write)",
                        "pull_tuning": tuning,
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "p50_ms": pct(50), "p99_ms": pct(99), "wall_s": wall,
-            "batched": {"batch": B, "value": batched_qps, "unit": "queries/s", "calls": nb,
-                        "same_queries_one_at_a_time": single_same_qps},
+            "batched": {"best": best, "sweep": batched},
             "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": 32, "d2h_bytes_per_step": 4 * n,
                     "steps": e2e_steps},
             "roofline": roof, "clocks": clk.summary(), "gpu_launches": agg["kernel_launches"],
             "phases_ms_per_query": {k: v / np_ for k, v in phases.items()},
             "profiled_ms_per_query": prof["step_ms"] / np_,
+            "switch": switch,
             "randomized_probe": randomized,
             "mixed_eps_topk": mixed,
             "serving": serving,
+            "serving_2p23": serving23,
             "work": {"walks_per_query": agg["walks"] / args.steps, "tree_nodes_per_query": agg["tree_nodes"] / args.steps,
                      "vectors_per_query": agg["vectors"] / args.steps,
                      "edge_gathers_per_query": agg["edge_gathers"] / args.steps}}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(n, s, d, qs, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(n, s, d, qs, args.cpu_walks_per_core)
     if world > 1:
         torch.distributed.barrier()
     print(json.dumps(line), flush=True)

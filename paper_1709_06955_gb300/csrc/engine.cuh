@@ -28,6 +28,23 @@ struct DevBuf {
         if (e == cudaSuccess) cap = nb; else cudaGetLastError();
         return e;
     }
+    // grows to at least `bytes`, keeping the first `keep` bytes (copied on stream s)
+    cudaError_t grow(size_t bytes, size_t keep, cudaStream_t s) {
+        if (bytes <= cap && p) return cudaSuccess;
+        void *q = nullptr;
+        const size_t nb = std::max<size_t>(256, bytes + bytes / 4);
+        cudaError_t e = cudaMalloc(&q, nb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        if (p && keep > 0) e = cudaMemcpyAsync(q, p, std::min(keep, cap), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && p) e = cudaStreamSynchronize(s);
+        if (p) cudaFree(p);
+        p = q;
+        cap = nb;
+        return e;
+    }
     void release() {
         if (p) cudaFree(p);
         p = nullptr;
@@ -65,7 +82,8 @@ struct Workspace {
     DevBuf t_key, t_node, t_parent, t_depth, t_query, t_weight, t_height, t_slot, t_gamma, t_G;
     DevBuf counts, offs, node_list, col_export, sched;  // level schedule: exported column nodes, uploaded plan
     DevBuf md_a, md_b, out_stage;                       // the two score buffers; host-output staging
-    DevBuf r_cnt, r_off, r_part, r_iwalk, r_ilen, r_iq, r_ik, r_fi[2], r_fn[2], r_keys[2], r_deg, r_pref, r_counts, r_ctr;
+    DevBuf r_cnt, r_off, r_part, r_iwalk, r_ilen, r_iq, r_ik, r_fi[2], r_fn[2], r_keys[2], r_deg, r_pref, r_counts,
+        r_counts2, r_ctr;
     DevBuf tk_hist, tk_state, tk_tie, tk_cid, tk_cval, tk_ids, tk_vals, tk_qk;
     // frontier engine: walk-prefix slots, switched flags, probes, frontier lists, next-level table, estimates
     DevBuf f_wslot, f_tsw, f_slot, f_misc, f_anc, f_deg, f_state, f_rsize, f_roff, f_acc, f_tab, f_work, f_wp,
@@ -92,7 +110,7 @@ struct Workspace {
                           &t_height, &t_slot, &t_gamma, &t_G, &counts, &offs, &node_list, &col_export,
                           &sched, &md_a, &md_b, &out_stage, &r_cnt, &r_off,
                           &r_part, &r_iwalk, &r_ilen, &r_iq, &r_ik, &r_fi[0], &r_fi[1], &r_fn[0], &r_fn[1],
-                          &r_keys[0], &r_keys[1], &r_deg, &r_pref, &r_counts, &r_ctr, &tk_hist, &tk_state, &tk_tie,
+                          &r_keys[0], &r_keys[1], &r_deg, &r_pref, &r_counts, &r_counts2, &r_ctr, &tk_hist, &tk_state, &tk_tie,
                           &tk_cid, &tk_cval, &tk_ids, &tk_vals, &tk_qk, &f_wslot, &f_tsw, &f_slot, &f_misc, &f_anc,
                           &f_deg, &f_state, &f_rsize, &f_roff, &f_acc, &f_tab, &f_work, &f_wp, &f_lp[0], &f_lp[1],
                           &f_lx[0], &f_lx[1], &f_lv[0], &f_lv[1], &f_cuts, &f_keys, &f_vals, &f_bcnt, &f_bpre};

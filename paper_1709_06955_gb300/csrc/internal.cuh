@@ -177,9 +177,9 @@ void launch_scatter_gamma(const int32_t *nodes, int32_t cnt, TrieTable t, float 
 void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, float *MD, ColLayout L,
                     int32_t h0, bool inherited, cudaStream_t s);
 // Parts of at most four sources: p1 (the first part of every group: bit 30 of the destination = set, else add)
-// then p2 (later parts: add).  Sources are -1 where absent; the destinations are columns < wdense.
-void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *p1dst, const int4 *p1src,
-                       int32_t np1, const int32_t *p2dst, const int4 *p2src, int32_t np2, cudaStream_t s);
+// then p2 (later parts: add).  Sources are -1 where absent.
+void launch_accumulate(int32_t n, float *B, ColLayout L, const int32_t *p1dst, const int4 *p1src, int32_t np1,
+                       const int32_t *p2dst, const int4 *p2src, int32_t np2, cudaStream_t s);
 // zeroes columns [c0, c0 + width) rounded up to a multiple of 4 (c0 a multiple of 4, inside the pitch)
 void launch_zero_cols(int32_t n, float *MD, ColLayout L, int32_t c0, int32_t width, cudaStream_t s);
 void launch_zero_split_rows(const DeviceGraph &g, float *MD, ColLayout L, int32_t width, cudaStream_t s);
@@ -280,15 +280,16 @@ struct RandLevel {
 };
 int64_t scan64_partials_needed(int64_t count);
 void launch_scan64(const long long *in, int64_t count, long long *partial, long long *out, cudaStream_t s);
-// Instances (walk w, prefix length i), i = 2..len; with walk_slot and t_sw given, only those whose prefix's tree
-// slot is flagged in t_sw (the probes the switch of Sec. 4.4 handed to Alg. 3).
-void launch_inst_count(const int32_t *lens, int32_t W, long long *cnt, const int32_t *walk_slot, const uint8_t *t_sw,
-                       int32_t l_max, cudaStream_t s);
-void launch_inst_init(const QueryBatch &q, const DeviceGraph &g, const int32_t *lens, int32_t W, int32_t l_max,
-                      const int32_t *walks, const long long *inst_off, int32_t *inst_walk, int32_t *inst_len,
-                      int32_t *inst_q, uint32_t *inst_k, int32_t *fr_inst, int32_t *fr_node,
+// Instances (walk w, prefix length i), i = 2..len, of the walks w0 .. w0+nw-1; with walk_slot and t_sw given, only
+// those whose prefix's tree slot is flagged in t_sw (the probes the switch of Sec. 4.4 handed to Alg. 3).
+void launch_inst_count(const int32_t *lens, int32_t w0, int32_t nw, long long *cnt, const int32_t *walk_slot,
+                       const uint8_t *t_sw, int32_t l_max, cudaStream_t s);
+void launch_inst_init(const QueryBatch &q, const DeviceGraph &g, const int32_t *lens, int32_t w0, int32_t nw,
+                      int32_t l_max, const int32_t *walks, const long long *inst_off, int32_t *inst_walk,
+                      int32_t *inst_len, int32_t *inst_q, uint32_t *inst_k, int32_t *fr_inst, int32_t *fr_node,
                       unsigned long long *fr_count, unsigned long long *keys, int64_t cap, int32_t *overflow,
                       const int32_t *walk_slot, const uint8_t *t_sw, cudaStream_t s);
+void launch_add_i32(int32_t *a, const int32_t *b, int64_t count, cudaStream_t s);  // a += b
 void launch_frontier_degree(const int32_t *fr_inst, const int32_t *fr_node, int64_t F, const int32_t *inst_len, int32_t j,
                             const int64_t *out_off, long long *deg, cudaStream_t s);
 void launch_rand_level(const DeviceGraph &g, const int32_t *walks, int32_t l_max, const int32_t *inst_walk,

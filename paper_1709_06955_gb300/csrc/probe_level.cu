@@ -120,116 +120,12 @@ void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, Tri
 // column already holds its heir's MD (the heir inherits the column); each group g adds (or, for a node
 // without heir, sets) the sum of its other children's columns: B[v][dst_g] (+)= sum of B[v][src], src in
 // srcs[off_g .. off_g+1).  No destination is a source of any group (the column assignment guarantees it), so
-// the groups are independent.  The groups touch most columns of every row, so the kernel streams rows
-// through shared memory: blocks of R rows are copied in with cp.async (the next block streams in while the
-// current one is updated), the destinations are updated there and the rows written back.
+// the groups are independent.  Groups are cut into parts of at most four sources.  One warp per row, lanes
+// over the parts; the later parts of groups with more than four sources add atomically after the row's first
+// parts are done.  Heirs and push heirs leave few parts per depth, so the kernel touches a few sectors of
+// each row in place (measured faster than streaming whole rows through shared memory at every batch width).
 // ------------------------------------------------------------------------------------------------
-constexpr int kAccThreads = 256;
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Shared-memory stage of R rows, segment-major: segment k (columns [256k, 256k + 256) of a grouped layout,
-// or all pitch columns of a node-major one) holds the R rows one after another, exactly as they lie in
-// global memory, so staging and write-back are linear copies.  Column c of row r sits at
-// cbase(c) + r * segw.
-struct AccStage {
-    int32_t nseg, segw, R;
-    bool grouped;
-    __device__ int32_t cbase(int32_t c) const {
-        return grouped ? (((c >> 8) * R) << 8) + (c & (kGroup - 1)) : c;  // kGroup = 256
-    }
-};
-static_assert(kGroup == 256, "AccStage::cbase assumes 256-column groups");
-
-// sum over a part's (at most four) sources of row r, and its destination column's address, inside a stage
-__device__ __forceinline__ float acc_part_sum(const float *buf, const AccStage &S, int4 sc, int32_t r) {
-    const int32_t rs = r * S.segw;
-    float sum = 0.f;
-    if (sc.x >= 0) sum += buf[S.cbase(sc.x) + rs];
-    if (sc.y >= 0) sum += buf[S.cbase(sc.y) + rs];
-    if (sc.z >= 0) sum += buf[S.cbase(sc.z) + rs];
-    if (sc.w >= 0) sum += buf[S.cbase(sc.w) + rs];
-    return sum;
-}
-
-__global__ void __launch_bounds__(kAccThreads) k_accumulate(int32_t n, float *B, ColLayout L, int32_t wstore,
-                                                            const int32_t *__restrict__ p1dst,
-                                                            const int4 *__restrict__ p1src, int32_t np1,
-                                                            const int32_t *__restrict__ p2dst,
-                                                            const int4 *__restrict__ p2src, int32_t np2, int32_t R) {
-    extern __shared__ float4 acc_sm4[];
-    const AccStage S{L.K > 0 ? L.K : 1, L.K > 0 ? kGroup : L.R, R, L.K > 0};
-    const int32_t stage_floats = S.nseg * S.segw * R;
-    const int32_t wseg = L.K > 0 ? (wstore + kGroup - 1) / kGroup : 1;  // segments written back
-    const int64_t step = (int64_t)gridDim.x * R;
-    // issue the copies of rows [r0, r0 + nr) into stage buffer `buf`
-    auto stage_in = [&](float *buf, int64_t r0, int32_t nr) {
-        const int32_t q4 = nr * S.segw / 4;
-        for (int32_t k = 0; k < S.nseg; ++k) {
-            const float4 *src = reinterpret_cast<const float4 *>(B + L.at(r0, k * S.segw));
-            float4 *dst = reinterpret_cast<float4 *>(buf + k * R * S.segw);
-            for (int32_t i = threadIdx.x; i < q4; i += blockDim.x) cp_async16(dst + i, src + i);
-        }
-        cp_async_commit();
-    };
-    float *const sm = reinterpret_cast<float *>(acc_sm4);
-    int64_t r0 = (int64_t)blockIdx.x * R;
-    int32_t cur = 0;
-    if (r0 < n) stage_in(sm, r0, (int32_t)min((int64_t)R, (int64_t)n - r0));
-    for (; r0 < n; r0 += step, cur ^= 1) {
-        float *buf = sm + cur * stage_floats;
-        const int32_t nr = (int32_t)min((int64_t)R, (int64_t)n - r0);
-        const int64_t r1 = r0 + step;
-        if (r1 < n) {  // the next block of rows streams in while this one is updated
-            stage_in(sm + (cur ^ 1) * stage_floats, r1, (int32_t)min((int64_t)R, (int64_t)n - r1));
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        // first parts: (part, row set) items; with fewer parts than threads, rsplit threads share a part's rows
-        const int32_t rsplit = max(1, min(nr, (int32_t)blockDim.x / max(1, np1)));
-        for (int32_t it = threadIdx.x; it < np1 * rsplit; it += blockDim.x) {
-            const int32_t pi = rsplit == 1 ? it : it % np1, part = rsplit == 1 ? 0 : it / np1;
-            const int32_t dd = __ldg(p1dst + pi);
-            const int4 sc = __ldg(p1src + pi);
-            const int32_t cd = S.cbase(dd & 0x3fffffff);
-            const bool set = (dd & (1 << 30)) != 0;  // no heir: the column is set, not added to
-            for (int32_t r = part; r < nr; r += rsplit) {
-                const float sum = acc_part_sum(buf, S, sc, r);
-                float &dst = buf[cd + r * S.segw];
-                dst = set ? sum : dst + sum;
-            }
-        }
-        if (np2 > 0) {  // later parts of groups with more than four sources add atomically
-            __syncthreads();
-            for (int32_t it = threadIdx.x; it < np2 * nr; it += blockDim.x) {
-                const int32_t pi = it % np2, r = it / np2;
-                const int4 sc = __ldg(p2src + pi);
-                atomicAdd(buf + S.cbase(__ldg(p2dst + pi)) + r * S.segw, acc_part_sum(buf, S, sc, r));
-            }
-        }
-        __syncthreads();
-        // write back the segments that can have changed (all of a node-major row block)
-        const int32_t q4 = nr * S.segw / 4;
-        for (int32_t k = 0; k < wseg; ++k) {
-            float4 *dst = reinterpret_cast<float4 *>(B + L.at(r0, k * S.segw));
-            const float4 *src = reinterpret_cast<const float4 *>(buf + k * R * S.segw);
-            for (int32_t i = threadIdx.x; i < q4; i += blockDim.x) dst[i] = src[i];
-        }
-        __syncthreads();  // the copies of a later iteration overwrite this buffer
-    }
-}
-
-// The same update straight in global memory, for wide rows: one warp per row, lanes over the parts; the
-// later parts add atomically after the first parts of the row are done.
-__device__ __forceinline__ float acc_part_sum_global(const float *B, const ColLayout &L, int64_t v, int4 sc) {
+__device__ __forceinline__ float acc_part_sum(const float *B, const ColLayout &L, int64_t v, int4 sc) {
     float sum = 0.f;
     if (sc.x >= 0) sum += B[L.at(v, sc.x)];
     if (sc.y >= 0) sum += B[L.at(v, sc.y)];
@@ -238,51 +134,33 @@ __device__ __forceinline__ float acc_part_sum_global(const float *B, const ColLa
     return sum;
 }
 
-__global__ void __launch_bounds__(256) k_accumulate_direct(int32_t n, float *B, ColLayout L,
-                                                           const int32_t *__restrict__ p1dst,
-                                                           const int4 *__restrict__ p1src, int32_t np1,
-                                                           const int32_t *__restrict__ p2dst,
-                                                           const int4 *__restrict__ p2src, int32_t np2) {
+__global__ void __launch_bounds__(256) k_accumulate(int32_t n, float *B, ColLayout L, const int32_t *__restrict__ p1dst,
+                                                    const int4 *__restrict__ p1src, int32_t np1,
+                                                    const int32_t *__restrict__ p2dst, const int4 *__restrict__ p2src,
+                                                    int32_t np2) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t v = warp; v < n; v += nwarps) {
         for (int32_t pi = lane; pi < np1; pi += 32) {
-            const float sum = acc_part_sum_global(B, L, v, __ldg(p1src + pi));
+            const float sum = acc_part_sum(B, L, v, __ldg(p1src + pi));
             const int32_t d = __ldg(p1dst + pi);
             float *dst = B + L.at(v, d & 0x3fffffff);
-            *dst = (d & (1 << 30)) ? sum : *dst + sum;
+            *dst = (d & (1 << 30)) ? sum : *dst + sum;  // bit 30: no heir, the column is set
         }
         if (np2 > 0) {
             __syncwarp();
             for (int32_t pi = lane; pi < np2; pi += 32)
-                atomicAdd(B + L.at(v, __ldg(p2dst + pi)), acc_part_sum_global(B, L, v, __ldg(p2src + pi)));
+                atomicAdd(B + L.at(v, __ldg(p2dst + pi)), acc_part_sum(B, L, v, __ldg(p2src + pi)));
             __syncwarp();
         }
     }
 }
 
-void launch_accumulate(int32_t n, float *B, ColLayout L, int32_t wdense, const int32_t *p1dst, const int4 *p1src,
-                       int32_t np1, const int32_t *p2dst, const int4 *p2src, int32_t np2, cudaStream_t s) {
+void launch_accumulate(int32_t n, float *B, ColLayout L, const int32_t *p1dst, const int4 *p1src, int32_t np1,
+                       const int32_t *p2dst, const int4 *p2src, int32_t np2, cudaStream_t s) {
     if (np1 <= 0) return;
-    const int32_t pitch = L.K > 0 ? L.K * kGroup : L.R;  // staged row width (a multiple of 4)
-    // staging pays while a row fits two stages of shared memory and the parts are many; rows over 96 KB, and
-    // depths with few parts (a few sectors of each row), are updated in place
-    // few parts (deep depths) touch a few sectors of each row: cheaper in place than streaming whole rows
-    if ((size_t)pitch * sizeof(float) > 96 * 1024 || (int64_t)(np1 + np2) * 40 < pitch) {
-        k_accumulate_direct<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(n, B, L, p1dst, p1src, np1, p2dst,
-                                                                             p2src, np2);
-        return;
-    }
-    // rows per stage: about 32 KB of rows, at least one; two stages per block (48 KB stages measured slower:
-    // fewer blocks per SM)
-    const int32_t R = std::max<int32_t>(1, std::min<int32_t>(256, 8192 / std::max(1, pitch)));
-    const size_t smem = 2 * sizeof(float) * (size_t)R * pitch;
-    const int32_t wstore = std::min(pitch, (wdense + 3) / 4 * 4);
-    cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / std::max<size_t>(1, smem)));
-    const int blocks = grid_for((int64_t)(n + R - 1) / R * kAccThreads, kAccThreads, per_sm);
-    k_accumulate<<<blocks, kAccThreads, smem, s>>>(n, B, L, wstore, p1dst, p1src, np1, p2dst, p2src, np2, R);
+    k_accumulate<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(n, B, L, p1dst, p1src, np1, p2dst, p2src, np2);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -40,6 +40,28 @@ probesim_status ps::fail_status(probesim_status st, const std::string &msg) { re
         }                                                                                              \
     } while (0)
 
+// an allocation of one walk range's buffers in the randomized PROBE: when it fails, the range is split
+#define PS_ALLOC_RANGE(expr)                                                                           \
+    do {                                                                                               \
+        cudaError_t _e = (expr);                                                                       \
+        if (_e != cudaSuccess) {                                                                       \
+            cudaGetLastError();                                                                        \
+            *too_big = true;                                                                           \
+            return fail(PROBESIM_E_NOMEM, std::string(#expr) + ": " + cudaGetErrorString(_e));         \
+        }                                                                                              \
+    } while (0)
+
+// an allocation of a batch's working buffers: when it fails on a call of several queries, the caller splits it
+#define PS_ALLOC(expr)                                                                                 \
+    do {                                                                                               \
+        cudaError_t _e = (expr);                                                                       \
+        if (_e != cudaSuccess) {                                                                       \
+            cudaGetLastError();                                                                        \
+            *too_big = B > 1;                                                                          \
+            return fail(PROBESIM_E_NOMEM, std::string(#expr) + ": " + cudaGetErrorString(_e));         \
+        }                                                                                              \
+    } while (0)
+
 #define PS_TRY(expr)                                  \
     do {                                              \
         probesim_status _s = (expr);                  \
@@ -503,14 +525,20 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         if (x.top != y.top) return x.top < y.top;
         return h_exp[5 * x.head] < h_exp[5 * y.head];
     });
-    std::vector<int32_t> top_min;  // per column: the smallest top depth of the chains holding it
+    // per column: the smallest top depth of the chains holding it, kept in a max segment tree over the
+    // columns (columns not opened yet hold INT32_MAX) so the first column above a depth is found in log time
+    int32_t seg_leaves = 1;
+    while (seg_leaves < std::max<int32_t>(1, (int32_t)chains.size())) seg_leaves <<= 1;
+    std::vector<int32_t> top_min(2 * (size_t)seg_leaves, INT32_MAX);
     for (const Chain &ch : chains) {
         // a column whose chain ends at depth d stays unused at depth d+1 too: there the accumulate sets it to
-        // the chain bottom's D, while other groups may still read what a chain starting at d+1 left in it
-        int32_t c = 0;
-        while (c < (int32_t)top_min.size() && top_min[c] <= ch.bottom + 1) ++c;
-        if (c == (int32_t)top_min.size()) top_min.push_back(ch.top);
-        top_min[c] = std::min(top_min[c], ch.top);
+        // the chain bottom's D, while other groups may still read what a chain starting at d+1 left in it.
+        // The chain takes the first column all of whose chains start below ch.bottom + 1.
+        int32_t i = 1;
+        while (i < seg_leaves) i = top_min[2 * i] > ch.bottom + 1 ? 2 * i : 2 * i + 1;
+        const int32_t c = i - seg_leaves;
+        top_min[i] = std::min(top_min[i], ch.top);
+        for (i >>= 1; i >= 1; i >>= 1) top_min[i] = std::max(top_min[2 * i], top_min[2 * i + 1]);
         int32_t last = ch.head;
         for (int32_t x = ch.head; x >= 0; x = heir[x]) col[x] = c, last = x;
         if (pheir[last] >= 0) col[pheir[last]] = c;
@@ -686,7 +714,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
             ph.begin(2);  // D of this depth's dense nodes, in place in B (the MD of depth d+1)
             const int32_t np1 = p1_at[d + 1] - p1_at[d], np2 = p2_at[d + 1] - p2_at[d];
             if (np1 > 0)
-                launch_accumulate(n, Bm, Lb, dw[d], d_sched + o_p1dst + p1_at[d],
+                launch_accumulate(n, Bm, Lb, d_sched + o_p1dst + p1_at[d],
                                   reinterpret_cast<const int4 *>(d_sched + o_p1src) + p1_at[d], np1,
                                   d_sched + o_p2dst + p2_at[d],
                                   reinterpret_cast<const int4 *>(d_sched + o_p2src) + p2_at[d], np2, st);
@@ -798,18 +826,21 @@ static probesim_status batch_walks(probesim_graph *g, Workspace *ws, const Batch
     return PROBESIM_OK;
 }
 
-// Randomized PROBE (Alg. 3) instances, one per (walk, prefix length i >= 2) -- or, with walk_slot and t_sw, only
-// those whose prefix's tree slot is flagged -- run level by level over hash-set frontiers.  Leaves the member
-// counts of the final levels in ws->r_counts ([B][n], internal ids).
-static probesim_status rand_instances(probesim_graph *g, Workspace *ws, const QueryBatch &qb, int32_t B, int32_t W,
-                                      int32_t max_len, const int32_t *walk_slot, const uint8_t *t_sw, int64_t &launches,
-                                      cudaStream_t st) {
+// Randomized PROBE (Alg. 3) instances of the walks w0 .. w1-1, one per (walk, prefix length i >= 2) -- or, with
+// walk_slot and t_sw, only those whose prefix's tree slot is flagged -- run level by level over hash-set
+// frontiers.  Adds the member counts of the final levels into counts ([B][n], internal ids).  An allocation that
+// fails sets *too_big (here: the walk range is too large) and returns PROBESIM_E_NOMEM.
+static probesim_status rand_range(probesim_graph *g, Workspace *ws, const QueryBatch &qb, int32_t B, int32_t w0,
+                                  int32_t w1, int32_t max_len, const int32_t *walk_slot, const uint8_t *t_sw,
+                                  int32_t *counts, int64_t &launches, cudaStream_t st, bool *too_big) {
+    *too_big = false;
+    const int32_t W = w1 - w0;
     const DeviceGraph &dg = g->dg;
-    const int32_t n = dg.n, L = g->cfg.l_max;
-    PS_CUDA(ws->r_cnt.ensure(sizeof(long long) * std::max(1, W)));
-    PS_CUDA(ws->r_off.ensure(sizeof(long long) * (W + 1)));
-    PS_CUDA(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(W)));
-    launch_inst_count(ws->lens.as<int32_t>(), W, ws->r_cnt.as<long long>(), walk_slot, t_sw, L, st);
+    const int32_t L = g->cfg.l_max;
+    PS_ALLOC_RANGE(ws->r_cnt.ensure(sizeof(long long) * std::max(1, W)));
+    PS_ALLOC_RANGE(ws->r_off.ensure(sizeof(long long) * (W + 1)));
+    PS_ALLOC_RANGE(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(W)));
+    launch_inst_count(ws->lens.as<int32_t>(), w0, W, ws->r_cnt.as<long long>(), walk_slot, t_sw, L, st);
     launch_scan64(ws->r_cnt.as<long long>(), W, ws->r_part.as<long long>(), ws->r_off.as<long long>(), st);
     launches += 4;
     long long *h_ll = reinterpret_cast<long long *>(ws->pin_s.as<char>() + 32768);
@@ -817,24 +848,22 @@ static probesim_status rand_instances(probesim_graph *g, Workspace *ws, const Qu
     PS_CUDA(cudaStreamSynchronize(st));
     const int64_t NI = h_ll[0];
     if (NI >= ((int64_t)1 << 31)) return fail(PROBESIM_E_INVALID, "too many probe instances in one call");
-    PS_CUDA(ws->r_counts.ensure(sizeof(int32_t) * (size_t)B * n));
-    PS_CUDA(cudaMemsetAsync(ws->r_counts.p, 0, sizeof(int32_t) * (size_t)B * n, st));
     if (NI == 0) return PROBESIM_OK;
-    PS_CUDA(ws->r_iwalk.ensure(sizeof(int32_t) * NI));
-    PS_CUDA(ws->r_ilen.ensure(sizeof(int32_t) * NI));
-    PS_CUDA(ws->r_iq.ensure(sizeof(int32_t) * NI));
-    PS_CUDA(ws->r_ik.ensure(sizeof(uint32_t) * NI));
-    PS_CUDA(ws->r_ctr.ensure(sizeof(unsigned long long) * 4));
+    PS_ALLOC_RANGE(ws->r_iwalk.ensure(sizeof(int32_t) * NI));
+    PS_ALLOC_RANGE(ws->r_ilen.ensure(sizeof(int32_t) * NI));
+    PS_ALLOC_RANGE(ws->r_iq.ensure(sizeof(int32_t) * NI));
+    PS_ALLOC_RANGE(ws->r_ik.ensure(sizeof(uint32_t) * NI));
+    PS_ALLOC_RANGE(ws->r_ctr.ensure(sizeof(unsigned long long) * 4));
     unsigned long long *d_fc = ws->r_ctr.as<unsigned long long>();
     int32_t *d_over = reinterpret_cast<int32_t *>(d_fc + 2);
     int cur = 0;
     int64_t cap = next_pow2(std::max<int64_t>(1024, 2 * NI));
-    PS_CUDA(ws->r_keys[cur].ensure(8 * (size_t)cap));
-    PS_CUDA(ws->r_fi[cur].ensure(4 * (size_t)NI));
-    PS_CUDA(ws->r_fn[cur].ensure(4 * (size_t)NI));
+    PS_ALLOC_RANGE(ws->r_keys[cur].ensure(8 * (size_t)cap));
+    PS_ALLOC_RANGE(ws->r_fi[cur].ensure(4 * (size_t)NI));
+    PS_ALLOC_RANGE(ws->r_fn[cur].ensure(4 * (size_t)NI));
     PS_CUDA(cudaMemsetAsync(ws->r_keys[cur].p, 0xFF, 8 * (size_t)cap, st));
     PS_CUDA(cudaMemsetAsync(d_fc, 0, sizeof(unsigned long long) * 4, st));
-    launch_inst_init(qb, dg, ws->lens.as<int32_t>(), W, L, ws->walks.as<int32_t>(), ws->r_off.as<long long>(),
+    launch_inst_init(qb, dg, ws->lens.as<int32_t>(), w0, W, L, ws->walks.as<int32_t>(), ws->r_off.as<long long>(),
                      ws->r_iwalk.as<int32_t>(), ws->r_ilen.as<int32_t>(), ws->r_iq.as<int32_t>(), ws->r_ik.as<uint32_t>(),
                      ws->r_fi[cur].as<int32_t>(), ws->r_fn[cur].as<int32_t>(), d_fc, ws->r_keys[cur].as<unsigned long long>(),
                      cap, d_over, walk_slot, t_sw, st);
@@ -846,9 +875,9 @@ static probesim_status rand_instances(probesim_graph *g, Workspace *ws, const Qu
     int64_t cur_cap = cap;
     for (int32_t j = 0; j + 2 <= max_len && F > 0; ++j) {
         // out-degree prefix sums of the frontier
-        PS_CUDA(ws->r_deg.ensure(sizeof(long long) * F));
-        PS_CUDA(ws->r_pref.ensure(sizeof(long long) * (F + 1)));
-        PS_CUDA(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(F)));
+        PS_ALLOC_RANGE(ws->r_deg.ensure(sizeof(long long) * F));
+        PS_ALLOC_RANGE(ws->r_pref.ensure(sizeof(long long) * (F + 1)));
+        PS_ALLOC_RANGE(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(F)));
         launch_frontier_degree(ws->r_fi[cur].as<int32_t>(), ws->r_fn[cur].as<int32_t>(), F, ws->r_ilen.as<int32_t>(), j,
                                dg.out_off, ws->r_deg.as<long long>(), st);
         launch_scan64(ws->r_deg.as<long long>(), F, ws->r_part.as<long long>(), ws->r_pref.as<long long>(), st);
@@ -859,9 +888,13 @@ static probesim_status rand_instances(probesim_graph *g, Workspace *ws, const Qu
         if (E <= 0) break;
         const int nx = cur ^ 1;
         const int64_t ncap = next_pow2(std::max<int64_t>(1024, 2 * E));
-        PS_CUDA(ws->r_keys[nx].ensure(8 * (size_t)ncap));
-        PS_CUDA(ws->r_fi[nx].ensure(4 * (size_t)E));
-        PS_CUDA(ws->r_fn[nx].ensure(4 * (size_t)E));
+        if ((size_t)(8 * ncap + 8 * E) > g->budget / 4 && w1 - w0 > 1) {  // a smaller walk range fits the budget
+            *too_big = true;
+            return fail(PROBESIM_E_NOMEM, "randomized PROBE level exceeds a quarter of the memory budget");
+        }
+        PS_ALLOC_RANGE(ws->r_keys[nx].ensure(8 * (size_t)ncap));
+        PS_ALLOC_RANGE(ws->r_fi[nx].ensure(4 * (size_t)E));
+        PS_ALLOC_RANGE(ws->r_fn[nx].ensure(4 * (size_t)E));
         PS_CUDA(cudaMemsetAsync(ws->r_keys[nx].p, 0xFF, 8 * (size_t)ncap, st));
         PS_CUDA(cudaMemsetAsync(d_fc, 0, sizeof(unsigned long long), st));
         RandLevel Lv;
@@ -877,7 +910,7 @@ static probesim_status rand_instances(probesim_graph *g, Workspace *ws, const Qu
         Lv.next_inst = ws->r_fi[nx].as<int32_t>();
         Lv.next_node = ws->r_fn[nx].as<int32_t>();
         Lv.next_count = d_fc;
-        Lv.counts = ws->r_counts.as<int32_t>();
+        Lv.counts = counts;
         Lv.overflow = d_over;
         Lv.j = j;
         launch_rand_level(dg, ws->walks.as<int32_t>(), L, ws->r_iwalk.as<int32_t>(), ws->r_ilen.as<int32_t>(),
@@ -895,6 +928,48 @@ static probesim_status rand_instances(probesim_graph *g, Workspace *ws, const Qu
     return PROBESIM_OK;
 }
 
+// All instances of the call (see rand_range), into ws->r_counts.  When the whole walk range does not fit, the
+// walks are taken in halves, quarters, ..., each counted into a side buffer added once the range completes, so
+// the integer member counts come out the same whatever the split.
+static probesim_status rand_instances(probesim_graph *g, Workspace *ws, const QueryBatch &qb, int32_t B, int32_t W,
+                                      int32_t max_len, const int32_t *walk_slot, const uint8_t *t_sw, int64_t &launches,
+                                      cudaStream_t st, bool *too_big) {
+    const size_t cn = (size_t)B * g->dg.n;
+    PS_ALLOC(ws->r_counts.ensure(sizeof(int32_t) * cn));
+    PS_CUDA(cudaMemsetAsync(ws->r_counts.p, 0, sizeof(int32_t) * cn, st));
+    bool oom = false;
+    probesim_status s = rand_range(g, ws, qb, B, 0, W, max_len, walk_slot, t_sw, ws->r_counts.as<int32_t>(), launches,
+                                   st, &oom);
+    if (s == PROBESIM_OK || !oom || W <= 1) {
+        if (oom) *too_big = B > 1;
+        return s;
+    }
+    DevBuf *big[] = {&ws->r_keys[0], &ws->r_keys[1], &ws->r_fi[0], &ws->r_fi[1], &ws->r_fn[0], &ws->r_fn[1],
+                     &ws->r_deg, &ws->r_pref};
+    for (DevBuf *b : big) b->release();
+    PS_CUDA(cudaMemsetAsync(ws->r_counts.p, 0, sizeof(int32_t) * cn, st));
+    PS_ALLOC(ws->r_counts2.ensure(sizeof(int32_t) * cn));
+    int32_t span = (W + 1) / 2;
+    for (int32_t w0 = 0; w0 < W;) {
+        const int32_t w1 = std::min(W, w0 + span);
+        PS_CUDA(cudaMemsetAsync(ws->r_counts2.p, 0, sizeof(int32_t) * cn, st));
+        s = rand_range(g, ws, qb, B, w0, w1, max_len, walk_slot, t_sw, ws->r_counts2.as<int32_t>(), launches, st, &oom);
+        if (s == PROBESIM_OK) {
+            launch_add_i32(ws->r_counts.as<int32_t>(), ws->r_counts2.as<int32_t>(), (int64_t)cn, st);
+            ++launches;
+            w0 = w1;
+        } else if (oom && span > 1) {
+            span = (span + 1) / 2;
+            for (DevBuf *b : big) b->release();
+        } else {
+            if (oom) *too_big = B > 1;
+            return s;
+        }
+    }
+    g_last_error.clear();  // the allocation failures that cut the walk range are not errors
+    return PROBESIM_OK;
+}
+
 // Randomized PROBE (Alg. 3) for every probe of Alg. 1: one instance per (walk, prefix length); the estimate is
 // the member count of the final levels divided by n_r.
 static probesim_status run_batch_rand(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t B,
@@ -906,7 +981,7 @@ static probesim_status run_batch_rand(probesim_graph *g, Workspace *ws, const pr
     int64_t launches = 0, walk_nodes = 0;
     int32_t max_len = 0;
     PS_TRY(batch_walks(g, ws, P, qb, &walk_nodes, &max_len, launches, st));
-    PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, nullptr, nullptr, launches, st));
+    PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, nullptr, nullptr, launches, st, too_big));
     launch_rand_finalize(g->dg.n, B, qb.node, ws->r_counts.as<int32_t>(), qb.inv_nr, g->dg.ext2int, d_out, st);
     ++launches;
     PS_CUDA(cudaGetLastError());
@@ -943,15 +1018,15 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     TrieTable t;
     t.cap = next_pow2(std::max<int64_t>(1024, 2 * (walk_nodes + B) + 64));
     const size_t cap = (size_t)t.cap;
-    PS_CUDA(ws->t_key.ensure(8 * cap));
-    PS_CUDA(ws->t_node.ensure(4 * cap));
-    PS_CUDA(ws->t_parent.ensure(4 * cap));
-    PS_CUDA(ws->t_depth.ensure(4 * cap));
-    PS_CUDA(ws->t_query.ensure(4 * cap));
-    PS_CUDA(ws->t_weight.ensure(4 * cap));
-    PS_CUDA(ws->t_height.ensure(4 * cap));
-    PS_CUDA(ws->f_wslot.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)P.W * L)));
-    PS_CUDA(ws->f_tsw.ensure(cap));
+    PS_ALLOC(ws->t_key.ensure(8 * cap));
+    PS_ALLOC(ws->t_node.ensure(4 * cap));
+    PS_ALLOC(ws->t_parent.ensure(4 * cap));
+    PS_ALLOC(ws->t_depth.ensure(4 * cap));
+    PS_ALLOC(ws->t_query.ensure(4 * cap));
+    PS_ALLOC(ws->t_weight.ensure(4 * cap));
+    PS_ALLOC(ws->t_height.ensure(4 * cap));
+    PS_ALLOC(ws->f_wslot.ensure(sizeof(int32_t) * std::max<int64_t>(1, (int64_t)P.W * L)));
+    PS_ALLOC(ws->f_tsw.ensure(cap));
     t.key = ws->t_key.as<unsigned long long>();
     t.node = ws->t_node.as<int32_t>();
     t.parent = ws->t_parent.as<int32_t>();
@@ -968,8 +1043,8 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     LaunchCounters *d_ctr = ws->ctr.as<LaunchCounters>();
     launch_trie_insert(dg, qb, P.W, L, ws->walks.as<int32_t>(), ws->lens.as<int32_t>(), t, d_ctr, st);
     // the probes: tree nodes of depth >= 2
-    PS_CUDA(ws->f_slot.ensure(sizeof(int32_t) * std::max<int64_t>(1, walk_nodes)));
-    PS_CUDA(ws->f_misc.ensure(64));
+    PS_ALLOC(ws->f_slot.ensure(sizeof(int32_t) * std::max<int64_t>(1, walk_nodes)));
+    PS_ALLOC(ws->f_misc.ensure(64));
     int32_t *d_np = ws->f_misc.as<int32_t>();
     unsigned long long *d_fctr = reinterpret_cast<unsigned long long *>(ws->f_misc.as<char>() + 8);
     PS_CUDA(cudaMemsetAsync(d_np, 0, 64, st));
@@ -987,11 +1062,11 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     // per-probe state, the two frontier lists, the estimate sums
     FrontierProbes PR;
     PR.P = NP;
-    PS_CUDA(ws->f_anc.ensure(sizeof(int32_t) * std::max(1, NP)));
-    PS_CUDA(ws->f_deg.ensure(sizeof(unsigned long long) * std::max(1, NP)));
-    PS_CUDA(ws->f_state.ensure(sizeof(int32_t) * std::max(1, NP)));
-    PS_CUDA(ws->f_rsize.ensure(sizeof(long long) * (NP + 1)));
-    PS_CUDA(ws->f_roff.ensure(sizeof(long long) * (NP + 1)));
+    PS_ALLOC(ws->f_anc.ensure(sizeof(int32_t) * std::max(1, NP)));
+    PS_ALLOC(ws->f_deg.ensure(sizeof(unsigned long long) * std::max(1, NP)));
+    PS_ALLOC(ws->f_state.ensure(sizeof(int32_t) * std::max(1, NP)));
+    PS_ALLOC(ws->f_rsize.ensure(sizeof(long long) * (NP + 1)));
+    PS_ALLOC(ws->f_roff.ensure(sizeof(long long) * (NP + 1)));
     PR.slot = ws->f_slot.as<int32_t>();
     PR.anc = ws->f_anc.as<int32_t>();
     PR.deg = ws->f_deg.as<unsigned long long>();
@@ -999,14 +1074,14 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     PR.rsize = ws->f_rsize.as<long long>();
     PR.roff = ws->f_roff.as<long long>();
     const size_t accn = (size_t)B * n;
-    PS_CUDA(ws->f_acc.ensure(sizeof(unsigned long long) * accn));
+    PS_ALLOC(ws->f_acc.ensure(sizeof(unsigned long long) * accn));
     PS_CUDA(cudaMemsetAsync(ws->f_acc.p, 0, sizeof(unsigned long long) * accn, st));
     // host tables: thr[w] = floor(c0 * w * n) in FP64 (the switch compares the integer out-degree sum with it),
     // pw[k] = sqrt(c)^k rounded to FP32 (Rule 2's factor)
     const size_t nthr = sw_mode ? (size_t)max_w + 1 : 0;
     const size_t tab_bytes = 256 * sizeof(float) + nthr * sizeof(long long);
-    PS_CUDA(ws->f_tab.ensure(tab_bytes));
-    PS_CUDA(ws->pin_q.ensure(tab_bytes));
+    PS_ALLOC(ws->f_tab.ensure(tab_bytes));
+    PS_ALLOC(ws->pin_q.ensure(tab_bytes));
     {
         char *h = ws->pin_q.as<char>();
         float *pw = reinterpret_cast<float *>(h);
@@ -1023,9 +1098,9 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     const long long *d_thr = sw_mode ? reinterpret_cast<const long long *>(ws->f_tab.as<char>() + 256 * sizeof(float)) : nullptr;
     int cur = 0;
     int64_t nF = NP;
-    PS_CUDA(ws->f_lp[cur].ensure(sizeof(int32_t) * std::max<int64_t>(1, nF)));
-    PS_CUDA(ws->f_lx[cur].ensure(sizeof(int32_t) * std::max<int64_t>(1, nF)));
-    PS_CUDA(ws->f_lv[cur].ensure(sizeof(long long) * std::max<int64_t>(1, nF)));
+    PS_ALLOC(ws->f_lp[cur].ensure(sizeof(int32_t) * std::max<int64_t>(1, nF)));
+    PS_ALLOC(ws->f_lx[cur].ensure(sizeof(int32_t) * std::max<int64_t>(1, nF)));
+    PS_ALLOC(ws->f_lv[cur].ensure(sizeof(long long) * std::max<int64_t>(1, nF)));
     auto list_of = [&](int k) {
         FrontierList F;
         F.p = ws->f_lp[k].as<int32_t>();
@@ -1040,9 +1115,9 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     int64_t switched = 0;
     for (int32_t j = 0; nF > 0; ++j) {
         const FrontierList F = list_of(cur);
-        PS_CUDA(ws->f_work.ensure(sizeof(long long) * (nF + 1)));
-        PS_CUDA(ws->f_wp.ensure(sizeof(long long) * (nF + 1)));
-        PS_CUDA(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(nF, NP))));
+        PS_ALLOC(ws->f_work.ensure(sizeof(long long) * (nF + 1)));
+        PS_ALLOC(ws->f_wp.ensure(sizeof(long long) * (nF + 1)));
+        PS_ALLOC(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(nF, NP))));
         long long *work = ws->f_work.as<long long>(), *wp = ws->f_wp.as<long long>();
         PS_CUDA(cudaMemsetAsync(d_fctr, 0, 2 * sizeof(unsigned long long), st));
         launch_fr_prune(F, nF, t, PR, dg.out_off, d_pw, g->cfg.eps_p, j, work, st);
@@ -1057,19 +1132,10 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
         PS_CUDA(cudaStreamSynchronize(st));
         const long long E = h_ll[0], T = h_ll[1];
         switched += h_ll[2];
-        const long long next_cap = std::max<long long>(1, h_ll[3]);  // distinct next entries <= sum of min(deg, n)
         ws->stats.edge_gathers += E;
         ws->stats.levels += 1;
         if (E == 0) break;  // nothing left to push: every remaining probe ended, switched or was pruned
         const int nx = cur ^ 1;
-        if ((size_t)next_cap * 16 > g->budget && B > 1) {  // a smaller batch may fit; one query just tries
-            *too_big = true;
-            return fail(PROBESIM_E_NOMEM, "frontier of one level exceeds the workspace budget");
-        }
-        PS_CUDA(ws->f_lp[nx].ensure(sizeof(int32_t) * next_cap));
-        PS_CUDA(ws->f_lx[nx].ensure(sizeof(int32_t) * next_cap));
-        PS_CUDA(ws->f_lv[nx].ensure(sizeof(long long) * next_cap));
-        const FrontierList Fn = list_of(nx);
         // passes over probe ranges whose regions fit pass_slots
         std::vector<int32_t> cuts{0};
         if (T > pass_slots) {
@@ -1094,7 +1160,7 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
         if (npass == 1) {
             fb[0] = 0; fb[1] = 0; fb[2] = nF; fb[3] = E;
         } else {
-            PS_CUDA(ws->f_cuts.ensure(sizeof(int32_t) * cuts.size() + sizeof(long long) * 2 * cuts.size()));
+            PS_ALLOC(ws->f_cuts.ensure(sizeof(int32_t) * cuts.size() + sizeof(long long) * 2 * cuts.size()));
             int32_t *d_cuts = ws->f_cuts.as<int32_t>();
             long long *d_fb = reinterpret_cast<long long *>(ws->f_cuts.as<char>() + ((sizeof(int32_t) * cuts.size() + 7) / 8 * 8));
             PS_CUDA(cudaMemcpyAsync(d_cuts, cuts.data(), sizeof(int32_t) * cuts.size(), cudaMemcpyHostToDevice, st));
@@ -1104,11 +1170,11 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
             PS_CUDA(cudaStreamSynchronize(st));
         }
         const long long tslots = std::min<long long>(T, pass_slots + n);
-        PS_CUDA(ws->f_keys.ensure(sizeof(int32_t) * std::max<long long>(1, tslots)));
-        PS_CUDA(ws->f_vals.ensure(sizeof(unsigned long long) * std::max<long long>(1, tslots)));
-        PS_CUDA(ws->f_bcnt.ensure(sizeof(long long) * (fr_compact_blocks(tslots) + 1)));
-        PS_CUDA(ws->f_bpre.ensure(sizeof(long long) * (fr_compact_blocks(tslots) + 1)));
-        PS_CUDA(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(
+        PS_ALLOC(ws->f_keys.ensure(sizeof(int32_t) * std::max<long long>(1, tslots)));
+        PS_ALLOC(ws->f_vals.ensure(sizeof(unsigned long long) * std::max<long long>(1, tslots)));
+        PS_ALLOC(ws->f_bcnt.ensure(sizeof(long long) * (fr_compact_blocks(tslots) + 1)));
+        PS_ALLOC(ws->f_bpre.ensure(sizeof(long long) * (fr_compact_blocks(tslots) + 1)));
+        PS_ALLOC(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(
                                       std::max<int64_t>(nF, NP), fr_compact_blocks(tslots)))));
         std::vector<long long> roff_cut(npass + 1, 0);
         if (npass > 1) {  // region offsets at the cuts
@@ -1139,17 +1205,20 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
             }
             launch_fr_expand(dg, t, PR, F, a, st);
             ++launches;
-            if (Tc > 0) {
+            if (Tc > 0) {  // count the pass's occupied slots, grow the next list to hold them, write them
                 const int64_t nb = fr_compact_blocks(Tc);
                 launch_fr_count(a.keys, Tc, ws->f_bcnt.as<long long>(), st);
                 launch_scan64(ws->f_bcnt.as<long long>(), nb, ws->r_part.as<long long>(), ws->f_bpre.as<long long>(), st);
-                launch_fr_write(a.keys, a.vals, Tc, PR.roff, cuts[c], cuts[c + 1], r0, ws->f_bpre.as<long long>(), Fn,
-                                out_n, next_cap, st);
-                launches += 5;
                 PS_CUDA(cudaMemcpyAsync(h_ll, ws->f_bpre.as<long long>() + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
                 PS_CUDA(cudaStreamSynchronize(st));
+                const long long need = std::max<long long>(1, out_n + h_ll[0]);
+                PS_ALLOC(ws->f_lp[nx].grow(sizeof(int32_t) * need, sizeof(int32_t) * out_n, st));
+                PS_ALLOC(ws->f_lx[nx].grow(sizeof(int32_t) * need, sizeof(int32_t) * out_n, st));
+                PS_ALLOC(ws->f_lv[nx].grow(sizeof(long long) * need, sizeof(long long) * out_n, st));
+                launch_fr_write(a.keys, a.vals, Tc, PR.roff, cuts[c], cuts[c + 1], r0, ws->f_bpre.as<long long>(),
+                                list_of(nx), out_n, need, st);
+                launches += 5;
                 out_n += h_ll[0];
-                if (out_n > next_cap) return fail(PROBESIM_E_CUDA, "internal: frontier larger than its bound");
             }
         }
         launch_fr_advance(t, PR, st);
@@ -1161,7 +1230,11 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     // Sec. 4.4: Alg. 3 for every walk through a switched tree node
     const int32_t *counts = nullptr;
     if (switched > 0) {
-        PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, t.walk_slot, t_sw, launches, st));
+        // the deterministic rounds' tables and lists are done with: their memory goes to Alg. 3's hash sets
+        for (DevBuf *b : {&ws->f_keys, &ws->f_vals, &ws->f_lp[0], &ws->f_lp[1], &ws->f_lx[0], &ws->f_lx[1],
+                          &ws->f_lv[0], &ws->f_lv[1], &ws->f_work, &ws->f_wp})
+            b->release();
+        PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, t.walk_slot, t_sw, launches, st, too_big));
         counts = ws->r_counts.as<int32_t>();
     }
     launch_fr_finalize(n, B, qb.node, ws->f_acc.as<unsigned long long>(), counts, qb.inv_nr, dg.ext2int, d_out, st);

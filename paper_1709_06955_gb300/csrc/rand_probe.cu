@@ -130,14 +130,20 @@ __device__ __forceinline__ bool inst_on(const int32_t *walk_slot, const uint8_t 
     return !walk_slot || t_sw[walk_slot[(int64_t)w * l_max + i - 1]];
 }
 
-// per walk: number of probes (len - 1, or the flagged ones)
-__global__ void k_inst_count(const int32_t *__restrict__ lens, int32_t W, long long *cnt,
+// per walk w0 + i of a walk range: number of probes (len - 1, or the flagged ones)
+__global__ void k_inst_count(const int32_t *__restrict__ lens, int32_t w0, int32_t nw, long long *cnt,
                              const int32_t *__restrict__ walk_slot, const uint8_t *__restrict__ t_sw, int32_t l_max) {
-    const int32_t w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= W) return;
+    const int32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 >= nw) return;
+    const int32_t w = w0 + i0;
     long long c = 0;
     for (int32_t i = 2; i <= lens[w]; ++i) c += inst_on(walk_slot, t_sw, l_max, w, i);
-    cnt[w] = c;
+    cnt[i0] = c;
+}
+
+__global__ void k_add_i32(int32_t *__restrict__ a, const int32_t *__restrict__ b, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] += b[i];
 }
 
 // instance (walk w, prefix length i) for i = 2..len; its level-0 frontier {u_i} goes into the table and list
@@ -175,15 +181,16 @@ __device__ __forceinline__ bool set_contains(const unsigned long long *keys, int
 }
 
 __global__ void k_inst_init(QueryBatch q, const int64_t *__restrict__ out_off, const int32_t *__restrict__ lens,
-                            int32_t W, int32_t l_max, const int32_t *__restrict__ walks,
+                            int32_t w0, int32_t nw, int32_t l_max, const int32_t *__restrict__ walks,
                             const long long *__restrict__ inst_off, int32_t *inst_walk, int32_t *inst_len,
                             int32_t *inst_q, uint32_t *inst_k, int32_t *fr_inst, int32_t *fr_node,
                             unsigned long long *fr_count, unsigned long long *keys, int64_t cap, int32_t *overflow,
                             const int32_t *__restrict__ walk_slot, const uint8_t *__restrict__ t_sw) {
-    const int32_t w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= W) return;
+    const int32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 >= nw) return;
+    const int32_t w = w0 + i0;
     const int32_t len = lens[w];
-    int64_t id = inst_off[w];
+    int64_t id = inst_off[i0];
     const int32_t b = walk_query(q.walk_base, q.B, w);
     const uint32_t k = (uint32_t)(q.walk_k0[b] + (w - q.walk_base[b]));
     for (int32_t i = 2; i <= len; ++i) {
@@ -307,19 +314,22 @@ __global__ void k_rand_finalize(int32_t n, int32_t B, const int32_t *__restrict_
     out[(int64_t)b * n + v] = s;
 }
 
-void launch_inst_count(const int32_t *lens, int32_t W, long long *cnt, const int32_t *walk_slot, const uint8_t *t_sw,
-                       int32_t l_max, cudaStream_t s) {
-    if (W > 0) k_inst_count<<<(W + 255) / 256, 256, 0, s>>>(lens, W, cnt, walk_slot, t_sw, l_max);
+void launch_inst_count(const int32_t *lens, int32_t w0, int32_t nw, long long *cnt, const int32_t *walk_slot,
+                       const uint8_t *t_sw, int32_t l_max, cudaStream_t s) {
+    if (nw > 0) k_inst_count<<<(nw + 255) / 256, 256, 0, s>>>(lens, w0, nw, cnt, walk_slot, t_sw, l_max);
 }
-void launch_inst_init(const QueryBatch &q, const DeviceGraph &g, const int32_t *lens, int32_t W, int32_t l_max,
-                      const int32_t *walks, const long long *inst_off, int32_t *inst_walk, int32_t *inst_len,
-                      int32_t *inst_q, uint32_t *inst_k, int32_t *fr_inst, int32_t *fr_node,
+void launch_inst_init(const QueryBatch &q, const DeviceGraph &g, const int32_t *lens, int32_t w0, int32_t nw,
+                      int32_t l_max, const int32_t *walks, const long long *inst_off, int32_t *inst_walk,
+                      int32_t *inst_len, int32_t *inst_q, uint32_t *inst_k, int32_t *fr_inst, int32_t *fr_node,
                       unsigned long long *fr_count, unsigned long long *keys, int64_t cap, int32_t *overflow,
                       const int32_t *walk_slot, const uint8_t *t_sw, cudaStream_t s) {
-    if (W > 0)
-        k_inst_init<<<(W + 255) / 256, 256, 0, s>>>(q, g.out_off, lens, W, l_max, walks, inst_off, inst_walk, inst_len,
-                                                    inst_q, inst_k, fr_inst, fr_node, fr_count, keys, cap, overflow,
-                                                    walk_slot, t_sw);
+    if (nw > 0)
+        k_inst_init<<<(nw + 255) / 256, 256, 0, s>>>(q, g.out_off, lens, w0, nw, l_max, walks, inst_off, inst_walk,
+                                                     inst_len, inst_q, inst_k, fr_inst, fr_node, fr_count, keys, cap,
+                                                     overflow, walk_slot, t_sw);
+}
+void launch_add_i32(int32_t *a, const int32_t *b, int64_t count, cudaStream_t s) {
+    if (count > 0) k_add_i32<<<grid_for(count, 256, 8), 256, 0, s>>>(a, b, count);
 }
 void launch_frontier_degree(const int32_t *fr_inst, const int32_t *fr_node, int64_t F, const int32_t *inst_len, int32_t j,
                             const int64_t *out_off, long long *deg, cudaStream_t s) {

@@ -9,6 +9,7 @@ that both the CUDA library's callers and the CPU oracle's tests use.
   duplicates rejected until m distinct edges exist.
 * ``rmat``: R-MAT (a, b, c, d) with 2^scale nodes; one quadrant choice per bit level; self-loops and
   duplicates removed, drawing until m distinct edges exist; a seeded node relabelling permutation.
+* ``rmat_device``: the same R-MAT recipe drawn on a CUDA device (torch), for the large benchmark graphs.
 * ``queries``: query nodes sampled uniformly from the nodes with in-degree >= 1 (Sec. 6.1).
 """
 import numpy as np
@@ -72,10 +73,40 @@ def rmat(scale, m, a=0.57, b=0.19, c=0.19, seed=1, relabel=True):
     return n, src.astype(np.int32), dst.astype(np.int32)
 
 
+def rmat_device(scale, m, a=0.57, b=0.19, c=0.19, seed=1, device="cuda"):
+    """The same R-MAT recipe as ``rmat``, drawn on a CUDA device with torch's seeded generator (for the large
+    benchmark graphs, where the host generator takes minutes).  Returns (n, src, dst) as int32 CUDA tensors.
+    The draws differ from ``rmat``'s, so the two give different graphs of the same distribution."""
+    import torch
+    n = 1 << scale
+    if m > n * (n - 1):
+        raise ValueError("m too large for a simple graph")
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    ab, abc = a + b, a + b + c
+    while keys.numel() < m:
+        k = max(4096, int((m - keys.numel()) * 1.25))
+        src = torch.zeros(k, dtype=torch.int64, device=device)
+        dst = torch.zeros(k, dtype=torch.int64, device=device)
+        for bit in range(scale):
+            r = torch.rand(k, generator=gen, device=device)
+            src |= (r >= ab).long() << bit
+            dst |= (((r >= a) & (r < ab)) | (r >= abc)).long() << bit
+        ok = src != dst
+        keys = torch.unique(torch.cat([keys, src[ok] * n + dst[ok]]))
+        del src, dst, ok
+    keys = keys[torch.randperm(keys.numel(), generator=gen, device=device)[:m]]
+    relabel = torch.randperm(n, generator=gen, device=device)
+    return n, relabel[keys // n].int(), relabel[keys % n].int()
+
+
 def queries(n, dst, count, seed=2):
     """``count`` query nodes drawn uniformly (without replacement when possible) from the nodes
     with at least one in-neighbour."""
     rng = np.random.default_rng(seed)
+    if type(dst).__module__.startswith("torch"):
+        dst = dst.cpu().numpy()
     indeg = np.bincount(np.asarray(dst, dtype=np.int64), minlength=n)
     cand = np.nonzero(indeg > 0)[0]
     if cand.size == 0:

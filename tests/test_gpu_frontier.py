@@ -196,6 +196,23 @@ def test_level_table_in_passes(rmat12):
     assert np.array_equal(ref, cut)
 
 
+def test_randomized_walk_ranges_under_a_small_budget(rmat12):
+    """Alg. 3 for the switched probes (and for the all-randomized mode) is cut into walk ranges when a level's
+    hash sets exceed the budget; the integer member counts, hence the estimates, do not change."""
+    from paper_1709_06955_gb300 import probesim
+    n, s, d, O = rmat12
+    qs = synth.queries(n, d, 3, seed=47)
+    Q = _q(qs, eps=0.15, query_ids=[41, 42, 43])
+    for kw in (dict(probe_mode=probesim.PROBE_SWITCH, c0=0.01), dict(probe_mode=probesim.PROBE_RANDOMIZED)):
+        G = gpu_graph(n, s, d, **kw)
+        ref = G.single_source(Q)
+        G.set_memory_budget(64 * 1024)
+        cut = G.single_source(Q)
+        G.set_memory_budget(0)
+        assert np.array_equal(ref, cut)
+        G.close()
+
+
 def test_edge_cases_frontier():
     """Queries without in-neighbours, l_max = 1 and 2, an edgeless node, with Rule 2 and the switch."""
     from paper_1709_06955_gb300 import probesim

@@ -84,8 +84,8 @@ def test_batched_equals_alone(cfg1):
 
 
 def test_wide_batch_equals_alone():
-    """256 queries in one call (R-MAT 2^14): the score matrices are over 24K columns wide, so the D accumulate
-    runs straight in global memory; sampled queries match the same queries alone (staged accumulate)."""
+    """256 queries in one call (R-MAT 2^14): the score matrices are over 24K columns wide (grouped layout with
+    many 256-column groups); sampled queries match the same queries alone (node-major matrices)."""
     n, s, d = synth.rmat(14, 16 << 14, seed=14)
     G = gpu_graph(n, s, d)
     qs = synth.queries(n, d, 256, seed=15)
