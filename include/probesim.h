@@ -150,6 +150,8 @@ typedef struct {
     int64_t table_passes;   /* passes over the frontier engine's per-level tables (more than one per level when
                                a table exceeds a quarter of the memory budget) */
     int64_t max_table_slots;/* largest per-level table, in slots of 12 bytes */
+    int64_t deferred;       /* probe ranges the frontier engine set aside at a level and resumed later, so that
+                               one level's frontier stays within an eighth of the memory budget */
 } probesim_stats;
 
 probesim_status probesim_set_profiling(probesim_graph *g, int32_t on);

@@ -86,8 +86,9 @@ struct Workspace {
         r_counts2, r_ctr;
     DevBuf tk_hist, tk_state, tk_tie, tk_cid, tk_cval, tk_ids, tk_vals, tk_qk;
     // frontier engine: walk-prefix slots, switched flags, probes, frontier lists, next-level table, estimates
-    DevBuf f_wslot, f_tsw, f_slot, f_misc, f_anc, f_deg, f_state, f_rsize, f_roff, f_acc, f_tab, f_work, f_wp,
-        f_lp[2], f_lx[2], f_lv[2], f_cuts, f_keys, f_vals, f_bcnt, f_bpre;
+    DevBuf f_wslot, f_tsw, f_slot, f_misc, f_anc, f_deg, f_state, f_rsize, f_roff, f_dsize, f_doff, f_acc, f_tab, f_wp,
+        f_lp[2], f_lx[2], f_lv[2], f_sp, f_sx, f_sv, f_cuts, f_keys, f_vals, f_bcnt, f_bpre;
+    bool f_table_clean = false;  // f_keys / f_vals hold only empty slots (every pass's compaction empties its slots)
     PinnedBuf pin_q;  // query arrays of one batch
     PinnedBuf pin_s;  // counters and schedule offsets (fixed size, allocated at creation)
     int profiling = 0;
@@ -112,9 +113,11 @@ struct Workspace {
                           &r_part, &r_iwalk, &r_ilen, &r_iq, &r_ik, &r_fi[0], &r_fi[1], &r_fn[0], &r_fn[1],
                           &r_keys[0], &r_keys[1], &r_deg, &r_pref, &r_counts, &r_counts2, &r_ctr, &tk_hist, &tk_state, &tk_tie,
                           &tk_cid, &tk_cval, &tk_ids, &tk_vals, &tk_qk, &f_wslot, &f_tsw, &f_slot, &f_misc, &f_anc,
-                          &f_deg, &f_state, &f_rsize, &f_roff, &f_acc, &f_tab, &f_work, &f_wp, &f_lp[0], &f_lp[1],
-                          &f_lx[0], &f_lx[1], &f_lv[0], &f_lv[1], &f_cuts, &f_keys, &f_vals, &f_bcnt, &f_bpre};
+                          &f_deg, &f_state, &f_rsize, &f_roff, &f_dsize, &f_doff, &f_acc, &f_tab, &f_wp, &f_lp[0],
+                          &f_lp[1], &f_lx[0], &f_lx[1], &f_lv[0], &f_lv[1], &f_sp, &f_sx, &f_sv, &f_cuts, &f_keys,
+                          &f_vals, &f_bcnt, &f_bpre};
         for (DevBuf *b : bufs) b->release();
+        f_table_clean = false;
         pin_q.release();
         pin_s.release();
         for (cudaEvent_t e : ev) cudaEventDestroy(e);

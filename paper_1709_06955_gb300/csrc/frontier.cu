@@ -11,7 +11,8 @@
 //            the probe's region of the next level's table -- open addressing over a power of two, or a
 //            dense slab of n slots when the probe's out-degree sum is a sizeable fraction of n -- or, at
 //            the probe's last level (j = q-2), straight into its query's estimate with weight w
-//   compact  the regions' occupied slots, in slot order, become H_{j+1}, still grouped by probe
+//   compact  the regions' occupied slots, in slot order, become H_{j+1}, still grouped by probe; the compaction
+//            empties the slots it reads, so the table needs no clearing between passes
 // Work items are (entry, out-edge) pairs balanced by prefix sums over the entries' out-degrees, so a hub's
 // out-list is spread over many threads and consecutive threads read consecutive out-edges.
 //
@@ -61,46 +62,59 @@ __global__ void k_fr_init(TrieTable t, FrontierProbes P, FrontierList F) {
     const int32_t s = P.slot[p];
     F.p[p] = p;
     F.x[p] = t.node[s];
-    F.val[p] = 1ll << kFixShift;
+    F.val[p] = 1.f;
     P.anc[p] = t.parent[s];
     P.deg[p] = 0;
     P.state[p] = 0;
 }
 
-// Rule 2 and the out-degree sums: work[f] = |O(x)| for kept entries, else 0
+// Rule 2 and the out-degree sums: work[f] = |O(x)| for kept entries, else 0.  Entries are grouped by probe, so
+// a warp sums each run of one probe's entries (a segmented shuffle scan) and the run's last lane adds it:
+// one atomic per run instead of one per entry on a counter that a large probe's millions of entries share.
 __global__ void k_fr_prune(FrontierList F, int64_t nF, TrieTable t, FrontierProbes P, const int64_t *__restrict__ out_off,
                            const float *__restrict__ pw, float eps_p, int32_t j, long long *__restrict__ work) {
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (f >= nF) return;
-    const int32_t p = F.p[f], x = F.x[f];
-    bool keep = true;
-    if (eps_p > 0.f) {
-        const int32_t q = t.depth[P.slot[p]];
-        keep = fx_to_f(F.val[f]) * pw[q - j - 1] > eps_p;
+    const bool valid = f < nF;
+    const int32_t p = valid ? F.p[f] : -1;
+    unsigned long long x = 0;
+    if (valid) {
+        const int32_t v = F.x[f];
+        bool keep = true;
+        if (eps_p > 0.f) {
+            const int32_t q = t.depth[P.slot[p]];
+            keep = F.val[f] * pw[q - j - 1] > eps_p;
+        }
+        x = keep ? (unsigned long long)(out_off[v + 1] - out_off[v]) : 0ull;
+        work[f] = (long long)x;
     }
-    const long long d = keep ? (long long)(out_off[x + 1] - out_off[x]) : 0;
-    work[f] = d;
-    if (d > 0) atomicAdd(&P.deg[p], (unsigned long long)d);
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        const int32_t q = __shfl_up_sync(0xffffffffu, p, o);
+        if (lane >= o && q == p) x += y;
+    }
+    const int32_t pn = __shfl_down_sync(0xffffffffu, p, 1);
+    if (valid && (lane == 31 || pn != p) && x > 0) atomicAdd(&P.deg[p], x);
 }
 
-// Per probe: the switch decision (Sec. 4.4) and the size of its region of the next level's table.
-// thr[w] = floor(c0 * w * n) (host FP64); the probe switches when its out-degree sum exceeds thr[w].
-// ctr[0] counts switched probes, ctr[1] sums min(out-degree sum, n) over the probes with a region.
-__global__ void k_fr_regions(TrieTable t, FrontierProbes P, int32_t j, int32_t n, const long long *__restrict__ thr,
-                             uint8_t *t_sw, unsigned long long *ctr) {
-    const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P.P) return;
+// Per probe of [p0, p1): the switch decision (Sec. 4.4), the size of its region of the next level's table and a
+// bound on its next level's entries.  thr[w] = floor(c0 * w * n) (host FP64); the probe switches when its
+// out-degree sum exceeds thr[w].  The decision is idempotent, so a probe range that resumes a level decides the
+// same again.
+__global__ void k_fr_regions(TrieTable t, FrontierProbes P, int32_t p0, int32_t p1, int32_t j, int32_t n,
+                             const long long *__restrict__ thr, uint8_t *t_sw) {
+    const int32_t p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= p1) return;
     const unsigned long long d = P.deg[p];
     P.deg[p] = 0;
-    long long r = 0;
+    long long r = 0, D = 0;
     if (d > 0) {
         const int32_t s = P.slot[p];
         if (thr && (long long)d > thr[t.weight[s]]) {
             P.state[p] |= kProbeSwitched;
             t_sw[s] = 1;
-            atomicAdd(&ctr[0], 1ull);
         } else if (j < t.depth[s] - 2) {
-            const long long D = (long long)d < (long long)n ? (long long)d : (long long)n;
+            D = (long long)d < (long long)n ? (long long)d : (long long)n;
             if (4 * D >= (long long)n) {  // dense slab: slot v holds node v
                 P.state[p] |= kProbeDense;
                 r = n;
@@ -109,10 +123,17 @@ __global__ void k_fr_regions(TrieTable t, FrontierProbes P, int32_t j, int32_t n
                 r = 2;
                 while (r < 2 * D) r <<= 1;
             }
-            atomicAdd(&ctr[1], (unsigned long long)D);
         }
     }
     P.rsize[p] = r;
+    P.dsize[p] = D;
+}
+
+__global__ void k_fr_count_switched(FrontierProbes P, unsigned long long *count) {
+    const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool sw = p < P.P && (P.state[p] & kProbeSwitched);
+    const unsigned m = __ballot_sync(0xffffffffu, sw);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(count, (unsigned long long)__popc(m));
 }
 
 // entries of switched probes do no deterministic work
@@ -160,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_fr_expand(DeviceGraph g, TrieTable
             const int32_t v = g.out_col[g.out_off[x] + e];
             const int32_t s = P.slot[p];
             if (v == t.node[P.anc[p]]) continue;  // level j excludes u_{q-j-1}
-            const long long c = f_to_fx(g.w[v] * fx_to_f(F.val[f]));
+            const long long c = f_to_fx(g.w[v] * F.val[f]);
             if (a.j == t.depth[s] - 2) {  // last level: weight * Score into the query's estimate
                 atomicAdd(a.acc + (int64_t)t.query[s] * a.n + v, (unsigned long long)(c * (long long)t.weight[s]));
                 continue;
@@ -207,17 +228,36 @@ __global__ void __launch_bounds__(kThreads) k_fr_count(const int32_t *__restrict
     if (threadIdx.x == 0) bcount[blockIdx.x] = s_cnt;
 }
 
-// writes the occupied slots of each block, in slot order, at out_base + bpre[block]
-__global__ void __launch_bounds__(kThreads) k_fr_write(const int32_t *__restrict__ keys,
-                                                       const unsigned long long *__restrict__ vals, long long T,
+// writes the occupied slots of each block, in slot order, at out_base + bpre[block], and empties them again, so
+// the table is clean for the next pass without a memset
+__global__ void __launch_bounds__(kThreads) k_fr_write(int32_t *__restrict__ keys, unsigned long long *__restrict__ vals,
+                                                       long long T,
                                                        const long long *__restrict__ roff, int32_t p0, int32_t p1,
                                                        long long rbase, const long long *__restrict__ bpre,
                                                        FrontierList out, long long out_base, long long out_cap) {
     __shared__ int s_warp[kThreads / 32];
     __shared__ long long s_run;
+    __shared__ int32_t s_plo, s_phi;
     const long long base = (long long)blockIdx.x * kCompactTile;
-    if (threadIdx.x == 0) s_run = out_base + bpre[blockIdx.x];
+    if (threadIdx.x == 0) {
+        s_run = out_base + bpre[blockIdx.x];
+        // the probes whose regions hold this block's first and last slots: the per-slot search stays between them
+        const long long last = min(T, base + kCompactTile) - 1;
+        int32_t lo = p0, hi = p1;
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (roff[mid] - rbase <= base) lo = mid; else hi = mid;
+        }
+        s_plo = lo;
+        hi = p1;
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (roff[mid] - rbase <= last) lo = mid; else hi = mid;
+        }
+        s_phi = lo + 1;
+    }
     __syncthreads();
+    const int32_t plo = s_plo, phi = s_phi;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = 0; r < kCompactTile; r += kThreads) {
         const long long k = base + r + threadIdx.x;
@@ -232,15 +272,19 @@ __global__ void __launch_bounds__(kThreads) k_fr_write(const int32_t *__restrict
         }
         const long long pos = s_run + before + __popc(m & ((1u << lane) - 1));
         if (occ && pos < out_cap) {  // the host sees a total above out_cap and fails the call
-            // the probe whose region holds slot k: largest p in [p0, p1) with roff[p] - rbase <= k
-            int32_t lo = p0, hi = p1;
+            // the probe whose region holds slot k: largest p in [plo, phi) with roff[p] - rbase <= k
+            int32_t lo = plo, hi = phi;
             while (hi - lo > 1) {
                 const int32_t mid = (lo + hi) >> 1;
                 if (roff[mid] - rbase <= k) lo = mid; else hi = mid;
             }
             out.p[pos] = lo;
             out.x[pos] = keys[k];
-            out.val[pos] = (long long)vals[k];
+            out.val[pos] = fx_to_f((long long)vals[k]);
+        }
+        if (occ) {
+            keys[k] = -1;
+            vals[k] = 0;
         }
         __syncthreads();
         if (threadIdx.x == 0) s_run += total;
@@ -248,16 +292,18 @@ __global__ void __launch_bounds__(kThreads) k_fr_write(const int32_t *__restrict
     }
 }
 
-// the next level excludes the next ancestor up
-__global__ void k_fr_advance(TrieTable t, FrontierProbes P) {
-    const int32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P.P) return;
+// the next level excludes the next ancestor up (probes [p0, p1))
+__global__ void k_fr_advance(TrieTable t, FrontierProbes P, int32_t p0, int32_t p1) {
+    const int32_t p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= p1) return;
     const int32_t a = P.anc[p];
     if (a >= 0) P.anc[p] = t.parent[a];
 }
 
-// first entry of each given probe in the probe-sorted frontier, and the work prefix there
+// for each given probe: its first entry in the probe-sorted frontier, the work prefix there, and the region and
+// entry-bound offsets at the probe
 __global__ void k_fr_bounds(const int32_t *__restrict__ fp, int64_t nF, const long long *__restrict__ wp,
+                            const long long *__restrict__ roff, const long long *__restrict__ doff,
                             const int32_t *__restrict__ probes, int32_t count, long long *__restrict__ out) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -267,8 +313,10 @@ __global__ void k_fr_bounds(const int32_t *__restrict__ fp, int64_t nF, const lo
         const int64_t mid = (lo + hi) >> 1;
         if (fp[mid] < p) lo = mid + 1; else hi = mid;
     }
-    out[2 * i] = lo;
-    out[2 * i + 1] = wp[lo];
+    out[4 * i] = lo;
+    out[4 * i + 1] = wp[lo];
+    out[4 * i + 2] = roff[p];
+    out[4 * i + 3] = doff[p];
 }
 
 // s(u, v) = (fixed-point deterministic sum + randomized member count) / n_r, s(u, u) = 1
@@ -302,9 +350,13 @@ void launch_fr_prune(FrontierList F, int64_t nF, TrieTable t, FrontierProbes P, 
                      float eps_p, int32_t j, long long *work, cudaStream_t s) {
     if (nF > 0) k_fr_prune<<<blocks_for(nF), kThreads, 0, s>>>(F, nF, t, P, out_off, pw, eps_p, j, work);
 }
-void launch_fr_regions(TrieTable t, FrontierProbes P, int32_t j, int32_t n, const long long *thr, uint8_t *t_sw,
-                       unsigned long long *ctr, cudaStream_t s) {
-    if (P.P > 0) k_fr_regions<<<blocks_for(P.P), kThreads, 0, s>>>(t, P, j, n, thr, t_sw, ctr);
+void launch_fr_regions(TrieTable t, FrontierProbes P, int32_t p0, int32_t p1, int32_t j, int32_t n, const long long *thr,
+                       uint8_t *t_sw, cudaStream_t s) {
+    if (p1 > p0) k_fr_regions<<<blocks_for(p1 - p0), kThreads, 0, s>>>(t, P, p0, p1, j, n, thr, t_sw);
+}
+void launch_fr_count_switched(FrontierProbes P, unsigned long long *count, cudaStream_t s) {
+    cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+    if (P.P > 0) k_fr_count_switched<<<blocks_for(P.P), kThreads, 0, s>>>(P, count);
 }
 void launch_fr_work(FrontierList F, int64_t nF, FrontierProbes P, long long *work, cudaStream_t s) {
     if (nF > 0) k_fr_work<<<blocks_for(nF), kThreads, 0, s>>>(F, nF, P, work);
@@ -320,19 +372,19 @@ int64_t fr_compact_blocks(long long T) { return (T + kCompactTile - 1) / kCompac
 void launch_fr_count(const int32_t *keys, long long T, long long *bcount, cudaStream_t s) {
     if (T > 0) k_fr_count<<<(unsigned)fr_compact_blocks(T), kThreads, 0, s>>>(keys, T, bcount);
 }
-void launch_fr_write(const int32_t *keys, const unsigned long long *vals, long long T, const long long *roff, int32_t p0,
+void launch_fr_write(int32_t *keys, unsigned long long *vals, long long T, const long long *roff, int32_t p0,
                      int32_t p1, long long rbase, const long long *bpre, FrontierList out, long long out_base,
                      long long out_cap, cudaStream_t s) {
     if (T > 0)
         k_fr_write<<<(unsigned)fr_compact_blocks(T), kThreads, 0, s>>>(keys, vals, T, roff, p0, p1, rbase, bpre, out,
                                                                        out_base, out_cap);
 }
-void launch_fr_advance(TrieTable t, FrontierProbes P, cudaStream_t s) {
-    if (P.P > 0) k_fr_advance<<<blocks_for(P.P), kThreads, 0, s>>>(t, P);
+void launch_fr_advance(TrieTable t, FrontierProbes P, int32_t p0, int32_t p1, cudaStream_t s) {
+    if (p1 > p0) k_fr_advance<<<blocks_for(p1 - p0), kThreads, 0, s>>>(t, P, p0, p1);
 }
-void launch_fr_bounds(const int32_t *fp, int64_t nF, const long long *wp, const int32_t *probes, int32_t count,
-                      long long *out, cudaStream_t s) {
-    if (count > 0) k_fr_bounds<<<blocks_for(count), kThreads, 0, s>>>(fp, nF, wp, probes, count, out);
+void launch_fr_bounds(const int32_t *fp, int64_t nF, const long long *wp, const long long *roff, const long long *doff,
+                      const int32_t *probes, int32_t count, long long *out, cudaStream_t s) {
+    if (count > 0) k_fr_bounds<<<blocks_for(count), kThreads, 0, s>>>(fp, nF, wp, roff, doff, probes, count, out);
 }
 void launch_fr_finalize(int32_t n, int32_t B, const int32_t *qnode, const unsigned long long *acc, const int32_t *counts,
                         const float *inv_nr, const int32_t *ext2int, float *out, cudaStream_t s) {

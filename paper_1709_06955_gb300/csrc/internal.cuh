@@ -224,19 +224,21 @@ struct FrontierProbes {
     unsigned long long *deg = nullptr;    // out-degree sum of the current level's kept entries
     int32_t *state = nullptr;             // kProbeSwitched | kProbeDense
     long long *rsize = nullptr;           // region slots in the next level's table
-    long long *roff = nullptr;            // [P+1] region offsets (exclusive prefix sums of rsize)
+    long long *roff = nullptr;            // [P+1] region offsets (exclusive prefix sums of rsize over a probe range)
+    long long *dsize = nullptr;           // bound on the next level's entries: min(out-degree sum, n)
+    long long *doff = nullptr;            // [P+1] its exclusive prefix sums over a probe range
 };
 struct FrontierList {  // entries of the frontiers, grouped by probe in probe order
     int32_t *p = nullptr;
     int32_t *x = nullptr;
-    long long *val = nullptr;             // score in 2^-44 units
+    float *val = nullptr;                 // score (the fixed-point sum of its level, rounded to FP32)
 };
 struct FrontierExpand {
     const long long *wp = nullptr;        // [nF+1] prefix sums of the entries' work (out-degrees)
     int64_t f_lo = 0, f_hi = 0;           // entries of this pass
     long long e_lo = 0, e_hi = 0;         // work items of this pass
     int32_t j = 0;                        // level
-    int32_t *keys = nullptr;              // next level's table: node per slot, -1 empty
+    int32_t *keys = nullptr;              // next level's table: node per slot, -1 empty (empty between passes)
     unsigned long long *vals = nullptr;   // score per slot (2^-44 units)
     long long rbase = 0;                  // table offset of this pass's first region
     unsigned long long *acc = nullptr;    // [B][n] estimates (2^-44 units, internal ids)
@@ -246,19 +248,21 @@ void launch_fr_list(TrieTable t, int32_t *slot, int32_t *count, cudaStream_t s);
 void launch_fr_init(TrieTable t, FrontierProbes P, FrontierList F, cudaStream_t s);
 void launch_fr_prune(FrontierList F, int64_t nF, TrieTable t, FrontierProbes P, const int64_t *out_off, const float *pw,
                      float eps_p, int32_t j, long long *work, cudaStream_t s);
-void launch_fr_regions(TrieTable t, FrontierProbes P, int32_t j, int32_t n, const long long *thr, uint8_t *t_sw,
-                       unsigned long long *ctr, cudaStream_t s);
+void launch_fr_regions(TrieTable t, FrontierProbes P, int32_t p0, int32_t p1, int32_t j, int32_t n, const long long *thr,
+                       uint8_t *t_sw, cudaStream_t s);
+void launch_fr_count_switched(FrontierProbes P, unsigned long long *count, cudaStream_t s);
 void launch_fr_work(FrontierList F, int64_t nF, FrontierProbes P, long long *work, cudaStream_t s);
 void launch_fr_expand(const DeviceGraph &g, TrieTable t, FrontierProbes P, FrontierList F, const FrontierExpand &a,
                       cudaStream_t s);
 int64_t fr_compact_blocks(long long T);
 void launch_fr_count(const int32_t *keys, long long T, long long *bcount, cudaStream_t s);
-void launch_fr_write(const int32_t *keys, const unsigned long long *vals, long long T, const long long *roff, int32_t p0,
+void launch_fr_write(int32_t *keys, unsigned long long *vals, long long T, const long long *roff, int32_t p0,
                      int32_t p1, long long rbase, const long long *bpre, FrontierList out, long long out_base,
                      long long out_cap, cudaStream_t s);
-void launch_fr_advance(TrieTable t, FrontierProbes P, cudaStream_t s);
-void launch_fr_bounds(const int32_t *fp, int64_t nF, const long long *wp, const int32_t *probes, int32_t count,
-                      long long *out, cudaStream_t s);
+void launch_fr_advance(TrieTable t, FrontierProbes P, int32_t p0, int32_t p1, cudaStream_t s);
+// per cut probe c: first entry, work prefix there, region offset and entry-bound offset
+void launch_fr_bounds(const int32_t *fp, int64_t nF, const long long *wp, const long long *roff, const long long *doff,
+                      const int32_t *probes, int32_t count, long long *out, cudaStream_t s);
 void launch_fr_finalize(int32_t n, int32_t B, const int32_t *qnode, const unsigned long long *acc, const int32_t *counts,
                         const float *inv_nr, const int32_t *ext2int, float *out, cudaStream_t s);
 

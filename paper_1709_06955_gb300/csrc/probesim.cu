@@ -1067,12 +1067,16 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     PS_ALLOC(ws->f_state.ensure(sizeof(int32_t) * std::max(1, NP)));
     PS_ALLOC(ws->f_rsize.ensure(sizeof(long long) * (NP + 1)));
     PS_ALLOC(ws->f_roff.ensure(sizeof(long long) * (NP + 1)));
+    PS_ALLOC(ws->f_dsize.ensure(sizeof(long long) * (NP + 1)));
+    PS_ALLOC(ws->f_doff.ensure(sizeof(long long) * (NP + 1)));
     PR.slot = ws->f_slot.as<int32_t>();
     PR.anc = ws->f_anc.as<int32_t>();
     PR.deg = ws->f_deg.as<unsigned long long>();
     PR.state = ws->f_state.as<int32_t>();
     PR.rsize = ws->f_rsize.as<long long>();
     PR.roff = ws->f_roff.as<long long>();
+    PR.dsize = ws->f_dsize.as<long long>();
+    PR.doff = ws->f_doff.as<long long>();
     const size_t accn = (size_t)B * n;
     PS_ALLOC(ws->f_acc.ensure(sizeof(unsigned long long) * accn));
     PS_CUDA(cudaMemsetAsync(ws->f_acc.p, 0, sizeof(unsigned long long) * accn, st));
@@ -1096,113 +1100,157 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     }
     const float *d_pw = ws->f_tab.as<float>();
     const long long *d_thr = sw_mode ? reinterpret_cast<const long long *>(ws->f_tab.as<char>() + 256 * sizeof(float)) : nullptr;
-    int cur = 0;
-    int64_t nF = NP;
-    PS_ALLOC(ws->f_lp[cur].ensure(sizeof(int32_t) * std::max<int64_t>(1, nF)));
-    PS_ALLOC(ws->f_lx[cur].ensure(sizeof(int32_t) * std::max<int64_t>(1, nF)));
-    PS_ALLOC(ws->f_lv[cur].ensure(sizeof(long long) * std::max<int64_t>(1, nF)));
+    // The deterministic rounds work on tasks: a probe range [p0, p1) at level j with its frontier entries.  A
+    // level whose next frontier might not fit the list budget processes the passes that fit and defers the other
+    // probes, with their level-j entries, to a stack; they resume once the processed range has run out.  Every
+    // probe's last-level pushes land in the estimate exactly once, whatever the split.
+    const long long pass_slots = std::max<long long>((long long)n, (long long)(g->budget / 4 / 12));
+    const long long list_cap = std::max<long long>((long long)n, (long long)(g->budget / 8 / 12));
     auto list_of = [&](int k) {
         FrontierList F;
         F.p = ws->f_lp[k].as<int32_t>();
         F.x = ws->f_lx[k].as<int32_t>();
-        F.val = ws->f_lv[k].as<long long>();
+        F.val = ws->f_lv[k].as<float>();
         return F;
     };
+    auto grow_list = [&](int k, long long need, long long keep, cudaStream_t s) -> cudaError_t {
+        cudaError_t e = ws->f_lp[k].grow(sizeof(int32_t) * need, sizeof(int32_t) * keep, s);
+        if (e == cudaSuccess) e = ws->f_lx[k].grow(sizeof(int32_t) * need, sizeof(int32_t) * keep, s);
+        if (e == cudaSuccess) e = ws->f_lv[k].grow(sizeof(float) * need, sizeof(float) * keep, s);
+        return e;
+    };
+    struct Task {
+        int32_t p0, p1, j;
+        long long at, count;  // entries on the deferral stack
+    };
+    std::vector<Task> stack;
+    long long stack_top = 0;
+    int cur = 0;
+    int64_t nF = NP;
+    int32_t p0 = 0, p1 = NP, j = 0;
+    PS_ALLOC(grow_list(cur, std::max<int64_t>(1, nF), 0, st));
     launch_fr_init(t, PR, list_of(cur), st);
     ++launches;
-    // the next level's table is cut into passes of at most this many slots (12 bytes each)
-    const long long pass_slots = std::max<long long>((long long)n, (long long)(g->budget / 4 / 12));
-    int64_t switched = 0;
-    for (int32_t j = 0; nF > 0; ++j) {
+    for (;;) {
+        if (nF == 0) {  // the range ran out: resume the last deferred one
+            if (stack.empty()) break;
+            const Task tk = stack.back();
+            stack.pop_back();
+            PS_ALLOC(grow_list(cur, std::max<long long>(1, tk.count), 0, st));
+            const FrontierList F = list_of(cur);
+            PS_CUDA(cudaMemcpyAsync(F.p, ws->f_sp.as<int32_t>() + tk.at, sizeof(int32_t) * tk.count, cudaMemcpyDeviceToDevice, st));
+            PS_CUDA(cudaMemcpyAsync(F.x, ws->f_sx.as<int32_t>() + tk.at, sizeof(int32_t) * tk.count, cudaMemcpyDeviceToDevice, st));
+            PS_CUDA(cudaMemcpyAsync(F.val, ws->f_sv.as<float>() + tk.at, sizeof(float) * tk.count, cudaMemcpyDeviceToDevice, st));
+            stack_top = tk.at;
+            p0 = tk.p0, p1 = tk.p1, j = tk.j, nF = tk.count;
+            ws->stats.deferred += 1;
+        }
         const FrontierList F = list_of(cur);
-        PS_ALLOC(ws->f_work.ensure(sizeof(long long) * (nF + 1)));
+        const int32_t np_ = p1 - p0;
         PS_ALLOC(ws->f_wp.ensure(sizeof(long long) * (nF + 1)));
-        PS_ALLOC(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(nF, NP))));
-        long long *work = ws->f_work.as<long long>(), *wp = ws->f_wp.as<long long>();
-        PS_CUDA(cudaMemsetAsync(d_fctr, 0, 2 * sizeof(unsigned long long), st));
-        launch_fr_prune(F, nF, t, PR, dg.out_off, d_pw, g->cfg.eps_p, j, work, st);
-        launch_fr_regions(t, PR, j, n, d_thr, t_sw, d_fctr, st);
-        launch_fr_work(F, nF, PR, work, st);
-        launch_scan64(work, nF, ws->r_part.as<long long>(), wp, st);
-        launch_scan64(PR.rsize, NP, ws->r_part.as<long long>(), PR.roff, st);
-        launches += 9;
+        PS_ALLOC(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(nF, np_))));
+        long long *wp = ws->f_wp.as<long long>();
+        launch_fr_prune(F, nF, t, PR, dg.out_off, d_pw, g->cfg.eps_p, j, wp, st);
+        launch_fr_regions(t, PR, p0, p1, j, n, d_thr, t_sw, st);
+        launch_fr_work(F, nF, PR, wp, st);
+        launch_scan64(wp, nF, ws->r_part.as<long long>(), wp, st);  // in place: wp[f] = first work item of entry f
+        launch_scan64(PR.rsize + p0, np_, ws->r_part.as<long long>(), PR.roff + p0, st);
+        launch_scan64(PR.dsize + p0, np_, ws->r_part.as<long long>(), PR.doff + p0, st);
+        launches += 12;
         PS_CUDA(cudaMemcpyAsync(h_ll, wp + nF, sizeof(long long), cudaMemcpyDeviceToHost, st));
-        PS_CUDA(cudaMemcpyAsync(h_ll + 1, PR.roff + NP, sizeof(long long), cudaMemcpyDeviceToHost, st));
-        PS_CUDA(cudaMemcpyAsync(h_ll + 2, d_fctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(h_ll + 1, PR.roff + p1, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(h_ll + 2, PR.doff + p1, sizeof(long long), cudaMemcpyDeviceToHost, st));
         PS_CUDA(cudaStreamSynchronize(st));
-        const long long E = h_ll[0], T = h_ll[1];
-        switched += h_ll[2];
+        const long long E = h_ll[0], T = h_ll[1], Dtot = h_ll[2];
         ws->stats.edge_gathers += E;
         ws->stats.levels += 1;
-        if (E == 0) break;  // nothing left to push: every remaining probe ended, switched or was pruned
+        if (E == 0) {  // nothing left to push: every probe of the range ended, switched or was pruned
+            nF = 0;
+            continue;
+        }
         const int nx = cur ^ 1;
-        // passes over probe ranges whose regions fit pass_slots
-        std::vector<int32_t> cuts{0};
+        // passes: probe ranges whose regions fit pass_slots (roff and doff are relative to p0)
+        std::vector<int32_t> cuts{p0};
         if (T > pass_slots) {
-            std::vector<long long> roff(NP + 1);
-            PS_CUDA(cudaMemcpyAsync(roff.data(), PR.roff, sizeof(long long) * (NP + 1), cudaMemcpyDeviceToHost, st));
+            std::vector<long long> roff(np_ + 1);
+            PS_CUDA(cudaMemcpyAsync(roff.data(), PR.roff + p0, sizeof(long long) * (np_ + 1), cudaMemcpyDeviceToHost, st));
             PS_CUDA(cudaStreamSynchronize(st));
-            int32_t p0 = 0;
-            while (p0 < NP) {
-                int32_t p1 = (int32_t)(std::upper_bound(roff.begin() + p0 + 1, roff.end(), roff[p0] + pass_slots) -
-                                       roff.begin()) - 1;
-                if (p1 <= p0) p1 = p0 + 1;
-                cuts.push_back(p1);
-                p0 = p1;
+            int32_t a = 0;
+            while (a < np_) {
+                int32_t b = (int32_t)(std::upper_bound(roff.begin() + a + 1, roff.end(), roff[a] + pass_slots) -
+                                      roff.begin()) - 1;
+                if (b <= a) b = a + 1;
+                cuts.push_back(p0 + b);
+                a = b;
             }
         } else {
-            cuts.push_back(NP);
+            cuts.push_back(p1);
         }
         const int32_t npass = (int32_t)cuts.size() - 1;
-        ws->stats.table_passes += npass;
-        ws->stats.max_table_slots = std::max<int64_t>(ws->stats.max_table_slots, T);
-        std::vector<long long> fb(2 * (size_t)(npass + 1));  // per cut: first entry, work prefix there
+        // per cut: first entry, work prefix, region offset, next-entry bound offset
+        std::vector<long long> cb(4 * (size_t)(npass + 1));
         if (npass == 1) {
-            fb[0] = 0; fb[1] = 0; fb[2] = nF; fb[3] = E;
+            cb = {0, 0, 0, 0, nF, E, T, Dtot};
         } else {
-            PS_ALLOC(ws->f_cuts.ensure(sizeof(int32_t) * cuts.size() + sizeof(long long) * 2 * cuts.size()));
+            PS_ALLOC(ws->f_cuts.ensure(sizeof(int32_t) * cuts.size() + 32 * cuts.size() + 16));
             int32_t *d_cuts = ws->f_cuts.as<int32_t>();
-            long long *d_fb = reinterpret_cast<long long *>(ws->f_cuts.as<char>() + ((sizeof(int32_t) * cuts.size() + 7) / 8 * 8));
+            long long *d_cb = reinterpret_cast<long long *>(ws->f_cuts.as<char>() + ((sizeof(int32_t) * cuts.size() + 15) / 16 * 16));
             PS_CUDA(cudaMemcpyAsync(d_cuts, cuts.data(), sizeof(int32_t) * cuts.size(), cudaMemcpyHostToDevice, st));
-            launch_fr_bounds(F.p, nF, wp, d_cuts, (int32_t)cuts.size(), d_fb, st);
+            launch_fr_bounds(F.p, nF, wp, PR.roff, PR.doff, d_cuts, (int32_t)cuts.size(), d_cb, st);
             ++launches;
-            PS_CUDA(cudaMemcpyAsync(fb.data(), d_fb, sizeof(long long) * fb.size(), cudaMemcpyDeviceToHost, st));
+            PS_CUDA(cudaMemcpyAsync(cb.data(), d_cb, sizeof(long long) * cb.size(), cudaMemcpyDeviceToHost, st));
             PS_CUDA(cudaStreamSynchronize(st));
         }
-        const long long tslots = std::min<long long>(T, pass_slots + n);
-        PS_ALLOC(ws->f_keys.ensure(sizeof(int32_t) * std::max<long long>(1, tslots)));
-        PS_ALLOC(ws->f_vals.ensure(sizeof(unsigned long long) * std::max<long long>(1, tslots)));
+        ws->stats.table_passes += npass;
+        ws->stats.max_table_slots = std::max<int64_t>(ws->stats.max_table_slots, T);
+        const long long tslots = std::max<long long>(1, std::min<long long>(T, pass_slots + n));
+        {
+            const void *k0 = ws->f_keys.p, *v0 = ws->f_vals.p;
+            PS_ALLOC(ws->f_keys.ensure(sizeof(int32_t) * tslots));
+            PS_ALLOC(ws->f_vals.ensure(sizeof(unsigned long long) * tslots));
+            if (ws->f_keys.p != k0 || ws->f_vals.p != v0 || !ws->f_table_clean) {  // new memory, or a failed call
+                PS_CUDA(cudaMemsetAsync(ws->f_keys.p, 0xFF, ws->f_keys.cap, st));   // left slots behind: clear it
+                PS_CUDA(cudaMemsetAsync(ws->f_vals.p, 0, ws->f_vals.cap, st));
+                ws->f_table_clean = true;
+            }
+        }
         PS_ALLOC(ws->f_bcnt.ensure(sizeof(long long) * (fr_compact_blocks(tslots) + 1)));
         PS_ALLOC(ws->f_bpre.ensure(sizeof(long long) * (fr_compact_blocks(tslots) + 1)));
         PS_ALLOC(ws->r_part.ensure(sizeof(long long) * scan64_partials_needed(std::max<int64_t>(
-                                      std::max<int64_t>(nF, NP), fr_compact_blocks(tslots)))));
-        std::vector<long long> roff_cut(npass + 1, 0);
-        if (npass > 1) {  // region offsets at the cuts
-            for (int32_t c = 0; c <= npass; ++c)
-                PS_CUDA(cudaMemcpyAsync(&roff_cut[c], PR.roff + cuts[c], sizeof(long long), cudaMemcpyDeviceToHost, st));
-            PS_CUDA(cudaStreamSynchronize(st));
-        } else {
-            roff_cut[1] = T;
-        }
+                                       std::max<int64_t>(nF, np_), fr_compact_blocks(tslots)))));
         long long out_n = 0;
+        int32_t pk = p1;  // probes [p0, pk) advance to level j + 1
         for (int32_t c = 0; c < npass; ++c) {
-            const long long r0 = roff_cut[c], Tc = roff_cut[c + 1] - r0;
+            const long long f_lo = cb[4 * c], e_lo = cb[4 * c + 1], r0 = cb[4 * c + 2], d0 = cb[4 * c + 3];
+            const long long f_hi = cb[4 * (c + 1)], e_hi = cb[4 * (c + 1) + 1], r1 = cb[4 * (c + 1) + 2],
+                            d1 = cb[4 * (c + 1) + 3];
+            if (out_n > 0 && out_n + (d1 - d0) > list_cap) {  // defer probes [cuts[c], p1) at level j
+                const long long cnt = nF - f_lo;
+                PS_ALLOC(ws->f_sp.grow(sizeof(int32_t) * (stack_top + cnt), sizeof(int32_t) * stack_top, st));
+                PS_ALLOC(ws->f_sx.grow(sizeof(int32_t) * (stack_top + cnt), sizeof(int32_t) * stack_top, st));
+                PS_ALLOC(ws->f_sv.grow(sizeof(float) * (stack_top + cnt), sizeof(float) * stack_top, st));
+                PS_CUDA(cudaMemcpyAsync(ws->f_sp.as<int32_t>() + stack_top, F.p + f_lo, sizeof(int32_t) * cnt, cudaMemcpyDeviceToDevice, st));
+                PS_CUDA(cudaMemcpyAsync(ws->f_sx.as<int32_t>() + stack_top, F.x + f_lo, sizeof(int32_t) * cnt, cudaMemcpyDeviceToDevice, st));
+                PS_CUDA(cudaMemcpyAsync(ws->f_sv.as<float>() + stack_top, F.val + f_lo, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, st));
+                stack.push_back({cuts[c], p1, j, stack_top, cnt});
+                stack_top += cnt;
+                pk = cuts[c];
+                break;
+            }
+            const long long Tc = r1 - r0;
             FrontierExpand a;
             a.wp = wp;
-            a.f_lo = fb[2 * c];
-            a.f_hi = fb[2 * (c + 1)];
-            a.e_lo = fb[2 * c + 1];
-            a.e_hi = fb[2 * (c + 1) + 1];
+            a.f_lo = f_lo;
+            a.f_hi = f_hi;
+            a.e_lo = e_lo;
+            a.e_hi = e_hi;
             a.j = j;
             a.keys = ws->f_keys.as<int32_t>();
             a.vals = ws->f_vals.as<unsigned long long>();
             a.rbase = r0;
             a.acc = ws->f_acc.as<unsigned long long>();
             a.n = n;
-            if (Tc > 0) {
-                PS_CUDA(cudaMemsetAsync(a.keys, 0xFF, sizeof(int32_t) * Tc, st));
-                PS_CUDA(cudaMemsetAsync(a.vals, 0, sizeof(unsigned long long) * Tc, st));
-            }
+            if (Tc > 0) ws->f_table_clean = false;  // until this pass's compaction has emptied its slots
             launch_fr_expand(dg, t, PR, F, a, st);
             ++launches;
             if (Tc > 0) {  // count the pass's occupied slots, grow the next list to hold them, write them
@@ -1212,27 +1260,32 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
                 PS_CUDA(cudaMemcpyAsync(h_ll, ws->f_bpre.as<long long>() + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
                 PS_CUDA(cudaStreamSynchronize(st));
                 const long long need = std::max<long long>(1, out_n + h_ll[0]);
-                PS_ALLOC(ws->f_lp[nx].grow(sizeof(int32_t) * need, sizeof(int32_t) * out_n, st));
-                PS_ALLOC(ws->f_lx[nx].grow(sizeof(int32_t) * need, sizeof(int32_t) * out_n, st));
-                PS_ALLOC(ws->f_lv[nx].grow(sizeof(long long) * need, sizeof(long long) * out_n, st));
+                PS_ALLOC(grow_list(nx, need, out_n, st));
                 launch_fr_write(a.keys, a.vals, Tc, PR.roff, cuts[c], cuts[c + 1], r0, ws->f_bpre.as<long long>(),
                                 list_of(nx), out_n, need, st);
                 launches += 5;
                 out_n += h_ll[0];
+                ws->f_table_clean = true;
             }
         }
-        launch_fr_advance(t, PR, st);
+        launch_fr_advance(t, PR, p0, pk, st);
         ++launches;
+        p1 = pk;
         nF = out_n;
         cur = nx;
+        ++j;
     }
+    launch_fr_count_switched(PR, d_fctr, st);
+    PS_CUDA(cudaMemcpyAsync(h_ll, d_fctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    const int64_t switched = h_ll[0];
     ws->stats.switched += switched;
     // Sec. 4.4: Alg. 3 for every walk through a switched tree node
     const int32_t *counts = nullptr;
     if (switched > 0) {
         // the deterministic rounds' tables and lists are done with: their memory goes to Alg. 3's hash sets
         for (DevBuf *b : {&ws->f_keys, &ws->f_vals, &ws->f_lp[0], &ws->f_lp[1], &ws->f_lx[0], &ws->f_lx[1],
-                          &ws->f_lv[0], &ws->f_lv[1], &ws->f_work, &ws->f_wp})
+                          &ws->f_lv[0], &ws->f_lv[1], &ws->f_wp, &ws->f_sp, &ws->f_sx, &ws->f_sv})
             b->release();
         PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, t.walk_slot, t_sw, launches, st, too_big));
         counts = ws->r_counts.as<int32_t>();

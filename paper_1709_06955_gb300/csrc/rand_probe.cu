@@ -125,6 +125,18 @@ __device__ __forceinline__ int32_t walk_query(const int32_t *walk_base, int32_t 
     return lo;
 }
 
+// A slot in an append list for each lane that calls it: the lanes executing the call together (__activemask) take
+// consecutive slots with one atomic on the shared counter, instead of one atomic each on the same address.
+__device__ __forceinline__ unsigned long long warp_append(unsigned long long *counter) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + (unsigned long long)__popc(mask & ((1u << lane) - 1u));
+}
+
 // instance (w, i) runs unless a filter is given and the tree slot of its prefix is not flagged
 __device__ __forceinline__ bool inst_on(const int32_t *walk_slot, const uint8_t *t_sw, int32_t l_max, int32_t w, int32_t i) {
     return !walk_slot || t_sw[walk_slot[(int64_t)w * l_max + i - 1]];
@@ -202,7 +214,7 @@ __global__ void k_inst_init(QueryBatch q, const int64_t *__restrict__ out_off, c
         const int32_t u = walks[(int64_t)w * l_max + i - 1];  // H_0 = {u_i}
         if (set_insert(keys, cap, ((unsigned long long)id << 32) | (uint32_t)u) < 0) atomicExch(overflow, 1);
         if (out_off[u + 1] > out_off[u]) {
-            const unsigned long long pos = atomicAdd(fr_count, 1ull);
+            const unsigned long long pos = warp_append(fr_count);
             fr_inst[pos] = (int32_t)id;
             fr_node[pos] = u;
         }
@@ -294,7 +306,7 @@ __global__ void __launch_bounds__(kLevelThreads) k_rand_level(DeviceGraph g, con
             if (i - 2 == L.j) {
                 atomicAdd(L.counts + (int64_t)b * g.n + x, 1);  // member of H_{i-1}: the probe's result
             } else if (g.out_off[x + 1] > g.out_off[x]) {    // only nodes with out-edges can expand
-                const unsigned long long pos = atomicAdd(L.next_count, 1ull);
+                const unsigned long long pos = warp_append(L.next_count);
                 L.next_inst[pos] = inst;
                 L.next_node[pos] = x;
             }

@@ -41,7 +41,8 @@ class Stats(C.Structure):
                 ("levels", C.c_int64), ("edge_gathers", C.c_int64), ("probe_launches", C.c_int64),
                 ("probe_ms", C.c_double), ("probe_bytes", C.c_double), ("kernel_launches", C.c_int64),
                 ("phase_ms", C.c_double * 12), ("max_columns", C.c_int64), ("probes", C.c_int64),
-                ("switched", C.c_int64), ("table_passes", C.c_int64), ("max_table_slots", C.c_int64)]
+                ("switched", C.c_int64), ("table_passes", C.c_int64), ("max_table_slots", C.c_int64),
+                ("deferred", C.c_int64)]
 
     PHASES = ["walks", "tree", "accumulate", "scatter", "zero_rows", "pull", "push", "gamma", "estimates",
               "host_schedule"]

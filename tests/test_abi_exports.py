@@ -44,7 +44,7 @@ def test_struct_layouts_match_header(lib):
     from paper_1709_06955_gb300 import probesim as P
     assert ctypes.sizeof(P.Config) == 40
     assert P.Query.eps.offset == 8 and ctypes.sizeof(P.Query) == 32
-    assert ctypes.sizeof(P.Stats) == 216
+    assert ctypes.sizeof(P.Stats) == 224
 
 
 def test_product_path_has_no_fallback(tmp_path):

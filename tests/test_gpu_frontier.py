@@ -186,13 +186,14 @@ def test_level_table_in_passes(rmat12):
     Q = _q(qs, eps=0.2, query_ids=[31, 32, 33, 34])
     ref = G.single_source(Q)
     whole = G.stats()
-    G.set_memory_budget(48 * 12 * n)  # passes of 12 n slots: a handful of dense regions each
+    G.set_memory_budget(48 * 12 * n)  # passes of 12 n slots, frontiers of 6 n entries before a range is deferred
     cut = G.single_source(Q)
     parts = G.stats()
     G.set_memory_budget(0)
     assert whole["max_table_slots"] > 12 * n  # the default budget took each level in one pass
-    assert whole["table_passes"] <= whole["levels"]
+    assert whole["table_passes"] <= whole["levels"] and whole["deferred"] == 0
     assert parts["table_passes"] > 2 * whole["table_passes"]
+    assert parts["deferred"] > 0
     assert np.array_equal(ref, cut)
 
 
