@@ -62,6 +62,8 @@ typedef struct {
     float c0;           /* switch constant of Sec. 4.4, >= 0 (used by PROBESIM_PROBE_SWITCH) */
     int32_t probe_mode; /* PROBESIM_PROBE_* */
     uint32_t seed;      /* first Philox key word of every walk and every randomized PROBE draw */
+    float shift;        /* added to every estimate s~(u, v), v != u (>= 0; 0 = none): the eps_t / 2 of Thm. 2 that
+                           centres Pruning Rule 1's one-sided error (see probesim_split_error) */
 } probesim_config;
 
 /* One query.  Its Philox key is (config.seed, query_id): walk k, step s draws counter (k, s, 0, 0), so a
@@ -75,8 +77,28 @@ typedef struct {
     int32_t walk_end;   /* divides by n_r); walk_end <= 0 means n_r.  0/0 is the full estimator */
 } probesim_query;
 
-/* Fills *cfg with c = 0.6, delta = 0.01, l_max = 64, eps_p = 0, c0 = 1, deterministic PROBE, seed = 3. */
+/* Fills *cfg with c = 0.6, delta = 0.01, l_max = 64, eps_p = 0, c0 = 1, deterministic PROBE, seed = 3, shift = 0. */
 probesim_status probesim_config_default(probesim_config *cfg);
+
+/* Thm. 2 (Sec. 4.1) bounds the error of Alg. 1 with both pruning rules, with probability 1 - delta, by
+ *     eps + T_p + eps_t / 2   when every estimate is shifted up by eps_t / 2 (Rule 1's error is one-sided),
+ *     eps + T_p + eps_t       without the shift,
+ * where T_p is Rule 2's term.  The paper states T_p = (1+eps)/(1-sqrt(c)) * eps_p from a per-probe bound of eps_p;
+ * that lemma's induction leaves out the score pruned at each later level, and the per-probe bound that holds is
+ * (i-1) * eps_p for the prefix of length i.  Summed over a sqrt(c)-walk's probes (E[l(l-1)/2] = sqrt(c)/(1-sqrt(c))^2
+ * for its geometric length l) it gives T_p = (1+eps) * sqrt(c)/(1-sqrt(c))^2 * eps_p.  This call splits a target
+ * error eps_a (0 < eps_a < 1) with the corrected T_p: eps = eps_a/2, T_p = eps_a/4 and Rule 1's term eps_a/4; l_max
+ * is the smallest walk length with sqrt(c)^l_max <= eps_t.  Pure host arithmetic (FP64). */
+typedef struct {
+    double eps;         /* sampling error of Alg. 1 (sets n_r) */
+    double eps_t;       /* Pruning Rule 1's termination parameter */
+    int32_t l_max;      /* nodes a walk keeps: ceil(ln eps_t / ln sqrt(c)), clamped to [1, 255] */
+    float eps_p;        /* Pruning Rule 2's parameter, rounded down to FP32 (the config's type) */
+    float shift;        /* eps_t / 2 with shift requested, else 0 (for probesim_config.shift) */
+    double bound;       /* the guaranteed error with the corrected T_p: <= eps_a */
+    double bound_paper; /* the same sum with the paper's T_p */
+} probesim_error_split;
+probesim_status probesim_split_error(double eps_a, double c, int32_t shift, probesim_error_split *out);
 
 /* Builds the device graph store from m directed edges src[e] -> dst[e] (Sec. 2.1: a directed simple
  * graph).  Self-loops and duplicate edges are dropped (a simple graph has neither) and the number kept
@@ -119,6 +141,18 @@ probesim_status probesim_single_source(probesim_graph *g, const probesim_query *
  * are set to -1 and 0.  1 <= q[i].k <= kmax <= n-1. */
 probesim_status probesim_topk(probesim_graph *g, const probesim_query *q, int32_t nq, int32_t kmax, int32_t *ids,
                               float *vals, void *stream);
+
+/* Pairwise Monte Carlo SimRank (Sec. 2.2, Eq. 3), the single-pair estimator the paper uses as the "expert" that
+ * gauges pooled top-k candidates: for pair i, r pairs of sqrt(c)-walks (Def. 3, at most l_max nodes each) from
+ * u[i] and v[i]; meets[i] counts the walk pairs whose j-th nodes coincide for some j, and est[i] = meets[i] / r
+ * (1 when u[i] = v[i]).  With r >= ln(1/delta) / (2 eps^2) the estimate is within eps of s(u, v) with probability
+ * 1 - delta.  Walk t from u[i] draws Philox counter (t, s, 0, 0) under key (config.seed, key_u[i]) at step s, the
+ * draws of walk t of a query with query_id key_u[i]; the walks from v[i] use key_v[i].  Inputs are host arrays of
+ * npairs entries (1 <= npairs <= 65535, 1 <= r < 2^32); meets and est are host or device arrays (est may be
+ * NULL). */
+probesim_status probesim_pair_mc(probesim_graph *g, const int32_t *u, const int32_t *v, const uint32_t *key_u,
+                                 const uint32_t *key_v, int32_t npairs, int64_t r, int64_t *meets, float *est,
+                                 void *stream);
 
 /* Per-call measurements of the last single_source/topk call on this graph.  When profiling is on, the
  * library records CUDA events around every launch of the PROBE level kernel (the dominant kernel) on the

@@ -319,17 +319,17 @@ __global__ void k_fr_bounds(const int32_t *__restrict__ fp, int64_t nF, const lo
     out[4 * i + 3] = doff[p];
 }
 
-// s(u, v) = (fixed-point deterministic sum + randomized member count) / n_r, s(u, u) = 1
+// s(u, v) = (fixed-point deterministic sum + randomized member count) / n_r + shift, s(u, u) = 1
 __global__ void k_fr_finalize(int32_t n, const int32_t *__restrict__ qnode, const unsigned long long *__restrict__ acc,
                               const int32_t *__restrict__ counts, const float *__restrict__ inv_nr,
-                              const int32_t *__restrict__ ext2int, float *__restrict__ out) {
+                              const int32_t *__restrict__ ext2int, float shift, float *__restrict__ out) {
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int32_t b = blockIdx.y;
     if (v >= n) return;
     const int64_t i = (int64_t)b * n + ext2int[v];
     long long tot = (long long)acc[i];
     if (counts) tot += (long long)counts[i] << kFixShift;
-    float s = fx_to_f(tot) * inv_nr[b];
+    float s = fx_to_f(tot) * inv_nr[b] + shift;
     if ((int32_t)v == qnode[b]) s = 1.f;
     out[(int64_t)b * n + v] = s;
 }
@@ -387,9 +387,9 @@ void launch_fr_bounds(const int32_t *fp, int64_t nF, const long long *wp, const 
     if (count > 0) k_fr_bounds<<<blocks_for(count), kThreads, 0, s>>>(fp, nF, wp, roff, doff, probes, count, out);
 }
 void launch_fr_finalize(int32_t n, int32_t B, const int32_t *qnode, const unsigned long long *acc, const int32_t *counts,
-                        const float *inv_nr, const int32_t *ext2int, float *out, cudaStream_t s) {
+                        const float *inv_nr, const int32_t *ext2int, float shift, float *out, cudaStream_t s) {
     dim3 grid(blocks_for(n), (unsigned)B);
-    k_fr_finalize<<<grid, kThreads, 0, s>>>(n, qnode, acc, counts, inv_nr, ext2int, out);
+    k_fr_finalize<<<grid, kThreads, 0, s>>>(n, qnode, acc, counts, inv_nr, ext2int, shift, out);
 }
 
 }  // namespace ps

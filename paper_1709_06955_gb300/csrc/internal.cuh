@@ -195,8 +195,9 @@ void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t d
                  const uint32_t *zmask, cudaStream_t s);
 void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, const float *inv_nr,
                   const float *MD, ColLayout L, cudaStream_t s);
+// out[q][v] = estimate + shift for v != u, out[q][u] = 1
 void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,
-                     ColLayout L, const int32_t *ext2int, float *out, cudaStream_t s);
+                     ColLayout L, const int32_t *ext2int, float shift, float *out, cudaStream_t s);
 // ids[i] = map[ids[i]] for ids[i] >= 0
 void launch_map_ids(int32_t *ids, int64_t count, const int32_t *map, cudaStream_t s);
 
@@ -264,7 +265,7 @@ void launch_fr_advance(TrieTable t, FrontierProbes P, int32_t p0, int32_t p1, cu
 void launch_fr_bounds(const int32_t *fp, int64_t nF, const long long *wp, const long long *roff, const long long *doff,
                       const int32_t *probes, int32_t count, long long *out, cudaStream_t s);
 void launch_fr_finalize(int32_t n, int32_t B, const int32_t *qnode, const unsigned long long *acc, const int32_t *counts,
-                        const float *inv_nr, const int32_t *ext2int, float *out, cudaStream_t s);
+                        const float *inv_nr, const int32_t *ext2int, float shift, float *out, cudaStream_t s);
 
 // randomized PROBE (rand_probe.cu)
 struct RandLevel {
@@ -300,7 +301,12 @@ void launch_rand_level(const DeviceGraph &g, const int32_t *walks, int32_t l_max
                        const int32_t *inst_len, const int32_t *inst_q, const uint32_t *inst_k, const uint32_t *qkey,
                        uint32_t seed, uint32_t t_keep, const RandLevel &L, cudaStream_t s);
 void launch_rand_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *counts, const float *inv_nr,
-                          const int32_t *ext2int, float *out, cudaStream_t s);
+                          const int32_t *ext2int, float shift, float *out, cudaStream_t s);
+
+// pairwise Monte Carlo (pair_mc.cu): meets[i] += walk pairs t in [0, r) from (pu[i], pv[i]) that meet (caller's ids)
+void launch_pair_mc(const DeviceGraph &g, const int32_t *pu, const int32_t *pv, const uint32_t *ku, const uint32_t *kv,
+                    int32_t npairs, int64_t r, int32_t l_max, uint32_t seed, uint32_t t_stop, unsigned long long *meets,
+                    cudaStream_t s);
 
 // device-side graph updates (graph_update.cu)
 struct UpdateBatchArgs {

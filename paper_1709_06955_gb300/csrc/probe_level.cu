@@ -245,24 +245,24 @@ void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieT
 }
 
 // ------------------------------------------------------------------------------------------------
-// finalize: out[q][v] = MD0[ext2int[v]][rho_slot(q)] for the caller's node id v, out[q][u_q] = 1 (s(u,u) = 1).
+// finalize: out[q][v] = MD0[ext2int[v]][rho_slot(q)] + shift for the caller's node id v, out[q][u_q] = 1 (s(u,u) = 1).
 // ------------------------------------------------------------------------------------------------
 __global__ void k_finalize(int32_t n, int32_t B, const int32_t *__restrict__ qnode, const int32_t *__restrict__ rho_slot,
                            const float *__restrict__ MD0, ColLayout L, const int32_t *__restrict__ ext2int,
-                           float *__restrict__ out) {
+                           float shift, float *__restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int32_t q = blockIdx.y;
     if (i >= n) return;
     const int32_t sl = rho_slot[q];
-    float v = sl >= 0 ? MD0[L.at(ext2int[i], sl)] : 0.f;
+    float v = (sl >= 0 ? MD0[L.at(ext2int[i], sl)] : 0.f) + shift;
     if ((int32_t)i == qnode[q]) v = 1.f;
     out[(int64_t)q * n + i] = v;
 }
 
 void launch_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *rho_slot, const float *MD0,
-                     ColLayout L, const int32_t *ext2int, float *out, cudaStream_t s) {
+                     ColLayout L, const int32_t *ext2int, float shift, float *out, cudaStream_t s) {
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)B);
-    k_finalize<<<grid, 256, 0, s>>>(n, B, qnode, rho_slot, MD0, L, ext2int, out);
+    k_finalize<<<grid, 256, 0, s>>>(n, B, qnode, rho_slot, MD0, L, ext2int, shift, out);
 }
 
 __global__ void k_map_ids(int32_t *ids, int64_t count, const int32_t *__restrict__ map) {

@@ -786,7 +786,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     float *MD0 = Bm;  // after the last swap, the super-roots' MD
     // 5. estimates: s(u, v) = MD(super-root)[v], s(u, u) = 1
     ph.begin(8);
-    launch_finalize(n, B, qb.node, d_rho, scount[0] > 0 ? MD0 : nullptr, lay[0], dg.ext2int, d_out, st);
+    launch_finalize(n, B, qb.node, d_rho, scount[0] > 0 ? MD0 : nullptr, lay[0], dg.ext2int, g->cfg.shift, d_out, st);
     ph.end();
     ++launches;
     PS_CUDA(cudaGetLastError());
@@ -982,7 +982,8 @@ static probesim_status run_batch_rand(probesim_graph *g, Workspace *ws, const pr
     int32_t max_len = 0;
     PS_TRY(batch_walks(g, ws, P, qb, &walk_nodes, &max_len, launches, st));
     PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, nullptr, nullptr, launches, st, too_big));
-    launch_rand_finalize(g->dg.n, B, qb.node, ws->r_counts.as<int32_t>(), qb.inv_nr, g->dg.ext2int, d_out, st);
+    launch_rand_finalize(g->dg.n, B, qb.node, ws->r_counts.as<int32_t>(), qb.inv_nr, g->dg.ext2int, g->cfg.shift, d_out,
+                         st);
     ++launches;
     PS_CUDA(cudaGetLastError());
     PS_CUDA(cudaStreamSynchronize(st));
@@ -1290,7 +1291,8 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
         PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, t.walk_slot, t_sw, launches, st, too_big));
         counts = ws->r_counts.as<int32_t>();
     }
-    launch_fr_finalize(n, B, qb.node, ws->f_acc.as<unsigned long long>(), counts, qb.inv_nr, dg.ext2int, d_out, st);
+    launch_fr_finalize(n, B, qb.node, ws->f_acc.as<unsigned long long>(), counts, qb.inv_nr, dg.ext2int, g->cfg.shift,
+                       d_out, st);
     ++launches;
     PS_CUDA(cudaGetLastError());
     PS_CUDA(cudaStreamSynchronize(st));
@@ -1356,6 +1358,33 @@ probesim_status probesim_config_default(probesim_config *cfg) {
     cfg->c0 = 1.f;
     cfg->probe_mode = PROBESIM_PROBE_DETERMINISTIC;
     cfg->seed = 3;
+    cfg->shift = 0.f;
+    return PROBESIM_OK;
+}
+
+probesim_status probesim_split_error(double eps_a, double c, int32_t shift, probesim_error_split *out) {
+    if (!out) return fail(PROBESIM_E_INVALID, "out is null");
+    if (!(eps_a > 0.0 && eps_a < 1.0)) return fail(PROBESIM_E_INVALID, "eps_a must lie in (0, 1)");
+    if (!(c > 0.0 && c < 1.0)) return fail(PROBESIM_E_INVALID, "c must lie in (0, 1)");
+    const double sc = std::sqrt(c);
+    const double eps = eps_a / 2.0, rest = eps_a / 2.0;
+    // Rule 1: error in [0, sqrt(c)^l_max] per walk, centred by the shift
+    const double eps_t = shift ? rest : rest / 2.0;
+    int32_t l_max = (int32_t)std::ceil(std::log(eps_t) / std::log(sc));
+    l_max = std::max(1, std::min(255, l_max));
+    // Rule 2: (1 + eps) * E[l (l - 1) / 2] * eps_p = rest / 2
+    const double per_walk = sc / ((1.0 - sc) * (1.0 - sc));
+    double ep = rest / 2.0 / ((1.0 + eps) * per_walk);
+    float epf = (float)ep;
+    if ((double)epf > ep) epf = std::nextafter(epf, 0.f);
+    out->eps = eps;
+    out->eps_t = eps_t;
+    out->l_max = l_max;
+    out->eps_p = epf;
+    out->shift = shift ? (float)(eps_t / 2.0) : 0.f;
+    const double r1 = std::pow(sc, (double)l_max) * (shift ? 0.5 : 1.0);
+    out->bound = eps + (1.0 + eps) * per_walk * (double)epf + r1;
+    out->bound_paper = eps + (1.0 + eps) / (1.0 - sc) * (double)epf + r1;
     return PROBESIM_OK;
 }
 
@@ -1372,7 +1401,8 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
     if (!(c.c > 0.0 && c.c < 1.0)) return fail(PROBESIM_E_INVALID, "c must lie in (0, 1)");
     if (!(c.delta > 0.0 && c.delta < 1.0)) return fail(PROBESIM_E_INVALID, "delta must lie in (0, 1)");
     if (c.l_max < 1 || c.l_max > 255) return fail(PROBESIM_E_INVALID, "l_max must lie in [1, 255]");
-    if (!(c.eps_p >= 0.f) || !(c.c0 >= 0.f)) return fail(PROBESIM_E_INVALID, "eps_p and c0 must be >= 0");
+    if (!(c.eps_p >= 0.f) || !(c.c0 >= 0.f) || !(c.shift >= 0.f))
+        return fail(PROBESIM_E_INVALID, "eps_p, c0 and shift must be >= 0");
     if (c.probe_mode < 0 || c.probe_mode > 2) return fail(PROBESIM_E_INVALID, "unknown probe_mode");
     std::vector<int32_t> hs, hd;
     PS_TRY(fetch_ids(src, m, hs));
@@ -1405,6 +1435,51 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
     }
     std::vector<uint64_t>().swap(g->keys);  // later updates merge on the device
     *out = g;
+    return PROBESIM_OK;
+}
+
+probesim_status probesim_pair_mc(probesim_graph *g, const int32_t *u, const int32_t *v, const uint32_t *key_u,
+                                 const uint32_t *key_v, int32_t npairs, int64_t r, int64_t *meets, float *est,
+                                 void *stream) {
+    if (!g || !u || !v || !key_u || !key_v || !meets) return fail(PROBESIM_E_INVALID, "null argument");
+    if (npairs < 1 || npairs > 65535) return fail(PROBESIM_E_INVALID, "npairs must lie in [1, 65535]");
+    if (r < 1 || r >= ((int64_t)1 << 32)) return fail(PROBESIM_E_INVALID, "r must lie in [1, 2^32)");
+    for (int32_t i = 0; i < npairs; ++i)
+        if (u[i] < 0 || u[i] >= g->dg.n || v[i] < 0 || v[i] >= g->dg.n) return fail(PROBESIM_E_RANGE, "node outside [0, n)");
+    std::lock_guard<std::mutex> lk(g->mu);
+    std::shared_lock<std::shared_mutex> sl(g->store_mu);
+    g_last_error.clear();
+    Workspace *ws = &g->ws0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t words = 4 * (size_t)npairs;
+    PS_CUDA(ws->pm_in.ensure(sizeof(int32_t) * words));
+    PS_CUDA(ws->pm_meets.ensure(sizeof(unsigned long long) * npairs));
+    PS_CUDA(ws->pin_q.ensure(std::max(sizeof(int32_t) * words, sizeof(unsigned long long) * npairs)));
+    int32_t *h = ws->pin_q.as<int32_t>();
+    std::memcpy(h, u, sizeof(int32_t) * npairs);
+    std::memcpy(h + npairs, v, sizeof(int32_t) * npairs);
+    std::memcpy(h + 2 * npairs, key_u, sizeof(uint32_t) * npairs);
+    std::memcpy(h + 3 * npairs, key_v, sizeof(uint32_t) * npairs);
+    int32_t *d = ws->pm_in.as<int32_t>();
+    PS_CUDA(cudaMemcpyAsync(d, h, sizeof(int32_t) * words, cudaMemcpyHostToDevice, st));
+    unsigned long long *dm = ws->pm_meets.as<unsigned long long>();
+    PS_CUDA(cudaMemsetAsync(dm, 0, sizeof(unsigned long long) * npairs, st));
+    launch_pair_mc(g->dg, d, d + npairs, reinterpret_cast<const uint32_t *>(d + 2 * npairs),
+                   reinterpret_cast<const uint32_t *>(d + 3 * npairs), npairs, r, g->cfg.l_max, g->cfg.seed, g->t_stop,
+                   dm, st);
+    PS_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> hm(npairs);
+    PS_CUDA(cudaMemcpyAsync(hm.data(), dm, sizeof(unsigned long long) * npairs, cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    std::vector<int64_t> m64(hm.begin(), hm.end());
+    std::vector<float> e(npairs);
+    for (int32_t i = 0; i < npairs; ++i) e[i] = u[i] == v[i] ? 1.f : (float)((double)hm[i] / (double)r);
+    if (is_device_ptr(meets)) PS_CUDA(cudaMemcpy(meets, m64.data(), sizeof(int64_t) * npairs, cudaMemcpyHostToDevice));
+    else std::memcpy(meets, m64.data(), sizeof(int64_t) * npairs);
+    if (est) {
+        if (is_device_ptr(est)) PS_CUDA(cudaMemcpy(est, e.data(), sizeof(float) * npairs, cudaMemcpyHostToDevice));
+        else std::memcpy(est, e.data(), sizeof(float) * npairs);
+    }
     return PROBESIM_OK;
 }
 

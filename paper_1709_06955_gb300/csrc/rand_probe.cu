@@ -317,11 +317,11 @@ __global__ void __launch_bounds__(kLevelThreads) k_rand_level(DeviceGraph g, con
 
 __global__ void k_rand_finalize(int32_t n, int32_t B, const int32_t *__restrict__ qnode,
                                 const int32_t *__restrict__ counts, const float *__restrict__ inv_nr,
-                                const int32_t *__restrict__ ext2int, float *__restrict__ out) {
+                                const int32_t *__restrict__ ext2int, float shift, float *__restrict__ out) {
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int32_t b = blockIdx.y;
     if (v >= n) return;
-    float s = (float)counts[(int64_t)b * n + ext2int[v]] * inv_nr[b];
+    float s = (float)counts[(int64_t)b * n + ext2int[v]] * inv_nr[b] + shift;
     if ((int32_t)v == qnode[b]) s = 1.f;
     out[(int64_t)b * n + v] = s;
 }
@@ -361,9 +361,9 @@ void launch_rand_level(const DeviceGraph &g, const int32_t *walks, int32_t l_max
                                                             seed, t_keep, L);
 }
 void launch_rand_finalize(int32_t n, int32_t B, const int32_t *qnode, const int32_t *counts, const float *inv_nr,
-                          const int32_t *ext2int, float *out, cudaStream_t s) {
+                          const int32_t *ext2int, float shift, float *out, cudaStream_t s) {
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)B);
-    k_rand_finalize<<<grid, 256, 0, s>>>(n, B, qnode, counts, inv_nr, ext2int, out);
+    k_rand_finalize<<<grid, 256, 0, s>>>(n, B, qnode, counts, inv_nr, ext2int, shift, out);
 }
 
 }  // namespace ps

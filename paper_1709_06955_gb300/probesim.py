@@ -22,13 +22,21 @@ EXPORTS = [
     "probesim_last_error", "probesim_topk_select_noalloc", "probesim_server_config_default",
     "probesim_server_create", "probesim_server_submit", "probesim_server_update", "probesim_server_poll",
     "probesim_server_get_stats", "probesim_server_destroy", "probesim_autotune", "probesim_get_tuning",
-    "probesim_set_memory_budget",
+    "probesim_set_memory_budget", "probesim_split_error", "probesim_pair_mc",
 ]
 
 
 class Config(C.Structure):
     _fields_ = [("c", C.c_double), ("delta", C.c_double), ("l_max", C.c_int32), ("eps_p", C.c_float),
-                ("c0", C.c_float), ("probe_mode", C.c_int32), ("seed", C.c_uint32)]
+                ("c0", C.c_float), ("probe_mode", C.c_int32), ("seed", C.c_uint32), ("shift", C.c_float)]
+
+
+class ErrorSplit(C.Structure):
+    _fields_ = [("eps", C.c_double), ("eps_t", C.c_double), ("l_max", C.c_int32), ("eps_p", C.c_float),
+                ("shift", C.c_float), ("bound", C.c_double), ("bound_paper", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Query(C.Structure):
@@ -106,6 +114,8 @@ def load(path=None):
     L.probesim_topk.argtypes = [vp, P(Query), C.c_int32, C.c_int32, vp, vp, vp]
     L.probesim_set_profiling.argtypes = [vp, C.c_int32]
     L.probesim_set_memory_budget.argtypes = [vp, C.c_double]
+    L.probesim_split_error.argtypes = [C.c_double, C.c_double, C.c_int32, P(ErrorSplit)]
+    L.probesim_pair_mc.argtypes = [vp, vp, vp, vp, vp, C.c_int32, C.c_int64, vp, vp, vp]
     L.probesim_get_stats.argtypes = [vp, P(Stats)]
     L.probesim_topk_select_noalloc.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int32, vp, vp, vp]
     L.probesim_server_config_default.argtypes = [P(ServerConfig)]
@@ -168,6 +178,14 @@ def default_config(**kw):
     for k, v in kw.items():
         setattr(cfg, k, v)
     return cfg
+
+
+def split_error(eps_a, c=0.6, shift=True):
+    """Thm. 2's split of a target error eps_a into eps, eps_t (l_max), eps_p and the eps_t/2 shift
+    (probesim_split_error).  Returns a dict; its l_max, eps_p and shift go into the graph's config."""
+    out = ErrorSplit()
+    _check(load().probesim_split_error(float(eps_a), float(c), 1 if shift else 0, C.byref(out)))
+    return out.as_dict()
 
 
 def make_queries(nodes, eps=0.1, k=50, query_ids=None, walk_begin=0, walk_end=0):
@@ -292,6 +310,21 @@ class Graph:
             vals = np.zeros((nq, kmax), np.float32)
         _check(load().probesim_topk(self._h, queries, nq, kmax, _ptr(ids), _ptr(vals), _stream(stream)))
         return ids, vals
+
+    def pair_mc(self, u, v, key_u, key_v, r, stream=None):
+        """Pairwise Monte Carlo SimRank of the pairs (u[i], v[i]) from r walk pairs each (probesim_pair_mc):
+        (meet counts int64, estimates float32)."""
+        u, v = _int32(u).ravel(), _int32(v).ravel()
+        ku = np.ascontiguousarray(key_u, dtype=np.uint32).ravel()
+        kv = np.ascontiguousarray(key_v, dtype=np.uint32).ravel()
+        npairs = u.size
+        if not (v.size == ku.size == kv.size == npairs):
+            raise ValueError("u, v, key_u and key_v must have one entry per pair")
+        meets = np.zeros(npairs, np.int64)
+        est = np.zeros(npairs, np.float32)
+        _check(load().probesim_pair_mc(self._h, _ptr(u), _ptr(v), _ptr(ku), _ptr(kv), npairs, int(r), _ptr(meets),
+                                       _ptr(est), _stream(stream)))
+        return meets, est
 
     def autotune(self, stream=None):
         """Times the pull launch shapes on this graph and keeps the fastest (probesim_autotune)."""
