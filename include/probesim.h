@@ -21,7 +21,8 @@
  *    released by probesim_graph_destroy).
  *  - A graph object may be used from several threads.  Direct query calls on one graph share one workspace
  *    and are serialised internally; a server's workers each own a workspace and run queries on one graph
- *    concurrently.  Update batches take the graph store exclusively, between queries.
+ *    concurrently.  An update batch builds the next version of the graph store beside the current one and
+ *    publishes it: a query sees the version current when it started, and neither waits for the other.
  *  - All arithmetic on the GPU is FP32 or integer; FP64 is used only on the host (n_r, thresholds).
  */
 #ifndef PROBESIM_H

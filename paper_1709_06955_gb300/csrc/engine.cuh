@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <memory>
 #include <mutex>
 #include <shared_mutex>
 #include <string>
@@ -76,6 +77,20 @@ struct PinnedBuf {
     T *as() const { return static_cast<T *>(p); }
 };
 
+// One version of the graph store.  A query holds the version it started with; an update batch builds the next
+// version beside it and publishes it, so queries never wait for updates nor updates for queries, and a version's
+// device memory is freed when its last reader lets go.
+struct StoreVersion {
+    DevBuf in_off, in_col, out_off, out_col, w, piece_v, piece_beg, piece_len, split_v;
+    std::shared_ptr<StoreVersion> base;  // set when this version reuses base's arrays (an update that changed nothing)
+    ps::DeviceGraph dg;
+    uint64_t epoch = 0;
+    ~StoreVersion() {
+        for (DevBuf *b : {&in_off, &in_col, &out_off, &out_col, &w, &piece_v, &piece_beg, &piece_len, &split_v})
+            b->release();
+    }
+};
+
 // Per-call device and pinned buffers; a graph owns one for direct calls, a server one per worker.
 struct Workspace {
     DevBuf qbuf, walks, lens, ctr;
@@ -93,6 +108,8 @@ struct Workspace {
     PinnedBuf pin_q;  // query arrays of one batch
     PinnedBuf pin_s;  // counters and schedule offsets (fixed size, allocated at creation)
     int profiling = 0;
+    std::shared_ptr<StoreVersion> snap;  // the store version of the call in progress
+    ps::DeviceGraph dg;                  // its device view
     std::vector<cudaEvent_t> ev;
     probesim_stats stats{};
     // a second stream for work of a depth that runs beside the pull (the push block, the tail tile), and the
@@ -131,14 +148,23 @@ struct Workspace {
 
 struct probesim_graph {
     std::mutex mu;              // serialises direct calls (they share ws0)
-    std::shared_mutex store_mu; // queries read the store shared; update batches take it exclusively
+    std::mutex update_mu;       // serialises update batches
+    std::mutex store_ptr_mu;    // guards the pointer to the current store version
+    std::shared_ptr<StoreVersion> store;
     probesim_config cfg{};
     uint32_t t_stop = 0;
     uint32_t t_keep = 0;
     int device = 0;
-    ps::DeviceGraph dg;
-    // device arrays of the graph store
-    DevBuf in_off, in_col, out_off, out_col, w, piece_v, piece_beg, piece_len, split_v, ext2int, int2ext;
+    int32_t n = 0;              // node count (fixed; updates change edges only)
+    DevBuf ext2int, int2ext;    // the id maps, shared by every store version
+    std::shared_ptr<StoreVersion> current() {
+        std::lock_guard<std::mutex> lk(store_ptr_mu);
+        return store;
+    }
+    void publish(std::shared_ptr<StoreVersion> v) {
+        std::lock_guard<std::mutex> lk(store_ptr_mu);
+        store.swap(v);  // the old version is released outside the lock, by whichever reader holds it last
+    }
     // sorted keys (dst << 32 | src) of the initial edge set, freed once the store is built
     std::vector<uint64_t> keys;
     std::vector<int32_t> h_ext2int;  // host copy of the id map (update batches are sorted by internal ids)
@@ -160,13 +186,13 @@ namespace ps {
 probesim_status fail_status(probesim_status st, const std::string &msg);
 // Checks a query array against the graph (ids, eps, k <= kmax when topk).
 probesim_status check_queries(const probesim_graph *g, const probesim_query *q, int32_t nq, bool topk, int32_t kmax);
-// Estimates and top-k of nq queries with workspace ws on stream st.  The caller owns ws and holds
-// g->store_mu shared.
-probesim_status single_source_core(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t nq,
-                                   float *scores, cudaStream_t st);
-probesim_status topk_core(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t nq, int32_t kmax,
-                          int32_t *ids, float *vals, cudaStream_t st);
-// Applies one update batch (takes g->store_mu exclusively).
+// Estimates and top-k of nq queries with workspace ws on stream st, over store version snap.  The caller owns ws.
+probesim_status single_source_core(probesim_graph *g, Workspace *ws, const std::shared_ptr<StoreVersion> &snap,
+                                   const probesim_query *q, int32_t nq, float *scores, cudaStream_t st);
+probesim_status topk_core(probesim_graph *g, Workspace *ws, const std::shared_ptr<StoreVersion> &snap,
+                          const probesim_query *q, int32_t nq, int32_t kmax, int32_t *ids, float *vals, cudaStream_t st);
+// Applies one update batch: builds the next store version from the current one and publishes it (serialised with
+// other update batches, never waiting for queries).
 probesim_status apply_updates(probesim_graph *g, const int32_t *src, const int32_t *dst, int64_t k, bool insert,
                               int64_t *applied, cudaStream_t st);
 int64_t num_walks_for(const probesim_graph *g, double eps);

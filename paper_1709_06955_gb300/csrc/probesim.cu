@@ -78,7 +78,7 @@ static int64_t num_walks(double c, double eps, double delta, int64_t n) {
     return (int64_t)std::ceil(3.0 * c / (eps * eps) * std::log((double)n / delta));
 }
 
-int64_t ps::num_walks_for(const probesim_graph *g, double eps) { return num_walks(g->cfg.c, eps, g->cfg.delta, g->dg.n); }
+int64_t ps::num_walks_for(const probesim_graph *g, double eps) { return num_walks(g->cfg.c, eps, g->cfg.delta, g->n); }
 
 static bool is_device_ptr(const void *p) {
     if (!p) return false;
@@ -176,48 +176,51 @@ static probesim_status upload_graph(probesim_graph *g, int32_t n, cudaStream_t s
     pv.resize(npieces);
     pb.resize(npieces);
     pl.resize(npieces);
-    PS_CUDA(g->in_off.ensure(sizeof(int64_t) * (n + 1)));
-    PS_CUDA(g->out_off.ensure(sizeof(int64_t) * (n + 1)));
-    PS_CUDA(g->in_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m)));
-    PS_CUDA(g->out_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m)));
-    PS_CUDA(g->w.ensure(sizeof(float) * n));
+    auto sv = std::make_shared<StoreVersion>();
+    PS_CUDA(sv->in_off.ensure(sizeof(int64_t) * (n + 1)));
+    PS_CUDA(sv->out_off.ensure(sizeof(int64_t) * (n + 1)));
+    PS_CUDA(sv->in_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m)));
+    PS_CUDA(sv->out_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m)));
+    PS_CUDA(sv->w.ensure(sizeof(float) * n));
     PS_CUDA(g->ext2int.ensure(sizeof(int32_t) * n));
     PS_CUDA(g->int2ext.ensure(sizeof(int32_t) * n));
-    PS_CUDA(g->piece_v.ensure(sizeof(int32_t) * std::max<size_t>(1, pv.size())));
-    PS_CUDA(g->piece_beg.ensure(sizeof(int64_t) * std::max<size_t>(1, pb.size())));
-    PS_CUDA(g->piece_len.ensure(sizeof(int32_t) * std::max<size_t>(1, pl.size())));
-    PS_CUDA(g->split_v.ensure(sizeof(int32_t) * std::max<size_t>(1, split.size())));
-    PS_CUDA(cudaMemcpyAsync(g->in_off.p, in_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(g->out_off.p, out_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    PS_CUDA(sv->piece_v.ensure(sizeof(int32_t) * std::max<size_t>(1, pv.size())));
+    PS_CUDA(sv->piece_beg.ensure(sizeof(int64_t) * std::max<size_t>(1, pb.size())));
+    PS_CUDA(sv->piece_len.ensure(sizeof(int32_t) * std::max<size_t>(1, pl.size())));
+    PS_CUDA(sv->split_v.ensure(sizeof(int32_t) * std::max<size_t>(1, split.size())));
+    PS_CUDA(cudaMemcpyAsync(sv->in_off.p, in_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(sv->out_off.p, out_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
     if (m > 0) {
-        PS_CUDA(cudaMemcpyAsync(g->in_col.p, in_col.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
-        PS_CUDA(cudaMemcpyAsync(g->out_col.p, out_col.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+        PS_CUDA(cudaMemcpyAsync(sv->in_col.p, in_col.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+        PS_CUDA(cudaMemcpyAsync(sv->out_col.p, out_col.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
     }
-    PS_CUDA(cudaMemcpyAsync(g->w.p, w.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(sv->w.p, w.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
     PS_CUDA(cudaMemcpyAsync(g->ext2int.p, ext2int.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
     PS_CUDA(cudaMemcpyAsync(g->int2ext.p, int2ext.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(g->piece_v.p, pv.data(), sizeof(int32_t) * pv.size(), cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(g->piece_beg.p, pb.data(), sizeof(int64_t) * pb.size(), cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(g->piece_len.p, pl.data(), sizeof(int32_t) * pl.size(), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(sv->piece_v.p, pv.data(), sizeof(int32_t) * pv.size(), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(sv->piece_beg.p, pb.data(), sizeof(int64_t) * pb.size(), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(sv->piece_len.p, pl.data(), sizeof(int32_t) * pl.size(), cudaMemcpyHostToDevice, st));
     if (!split.empty())
-        PS_CUDA(cudaMemcpyAsync(g->split_v.p, split.data(), sizeof(int32_t) * split.size(), cudaMemcpyHostToDevice, st));
+        PS_CUDA(cudaMemcpyAsync(sv->split_v.p, split.data(), sizeof(int32_t) * split.size(), cudaMemcpyHostToDevice, st));
     PS_CUDA(cudaStreamSynchronize(st));
-    DeviceGraph &d = g->dg;
+    DeviceGraph &d = sv->dg;
     d.n = n;
     d.m = m;
-    d.in_off = g->in_off.as<int64_t>();
-    d.in_col = g->in_col.as<int32_t>();
-    d.out_off = g->out_off.as<int64_t>();
-    d.out_col = g->out_col.as<int32_t>();
-    d.w = g->w.as<float>();
+    d.in_off = sv->in_off.as<int64_t>();
+    d.in_col = sv->in_col.as<int32_t>();
+    d.out_off = sv->out_off.as<int64_t>();
+    d.out_col = sv->out_col.as<int32_t>();
+    d.w = sv->w.as<float>();
     d.n_pieces = (int64_t)pv.size();
-    d.piece_v = g->piece_v.as<int32_t>();
-    d.piece_beg = g->piece_beg.as<int64_t>();
-    d.piece_len = g->piece_len.as<int32_t>();
+    d.piece_v = sv->piece_v.as<int32_t>();
+    d.piece_beg = sv->piece_beg.as<int64_t>();
+    d.piece_len = sv->piece_len.as<int32_t>();
     d.n_split = (int32_t)split.size();
-    d.split_v = g->split_v.as<int32_t>();
+    d.split_v = sv->split_v.as<int32_t>();
     d.ext2int = g->ext2int.as<int32_t>();
     d.int2ext = g->int2ext.as<int32_t>();
+    g->n = n;
+    g->publish(sv);
     return PROBESIM_OK;
 }
 
@@ -252,7 +255,7 @@ static probesim_status plan_batch(probesim_graph *g, const probesim_query *q, in
     P.inv_nr.resize(B);
     int64_t W = 0;
     for (int32_t b = 0; b < B; ++b) {
-        const int64_t nr = num_walks(g->cfg.c, q[b].eps, g->cfg.delta, g->dg.n);
+        const int64_t nr = num_walks(g->cfg.c, q[b].eps, g->cfg.delta, g->n);
         const int64_t kb = std::max<int64_t>(0, q[b].walk_begin);
         const int64_t ke = q[b].walk_end <= 0 ? nr : std::min<int64_t>(q[b].walk_end, nr);
         P.node[b] = q[b].node;
@@ -346,7 +349,7 @@ struct PhaseTimer {
 static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t B, float *d_out,
                                  cudaStream_t st, bool *too_big) {
     *too_big = false;
-    const DeviceGraph &dg = g->dg;
+    const DeviceGraph &dg = ws->dg;
     const int32_t n = dg.n;
     const int32_t L = g->cfg.l_max;
     BatchPlan P;
@@ -813,7 +816,7 @@ static probesim_status batch_walks(probesim_graph *g, Workspace *ws, const Batch
     PS_CUDA(ws->ctr.ensure(sizeof(LaunchCounters)));
     LaunchCounters *d_ctr = ws->ctr.as<LaunchCounters>();
     PS_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(LaunchCounters), st));
-    launch_walks(g->dg, qb, P.W, L, g->t_stop, g->cfg.seed, ws->walks.as<int32_t>(), ws->lens.as<int32_t>(), false,
+    launch_walks(ws->dg, qb, P.W, L, g->t_stop, g->cfg.seed, ws->walks.as<int32_t>(), ws->lens.as<int32_t>(), false,
                  d_ctr, st);
     ++launches;
     LaunchCounters *h_ctr = ws->pin_s.as<LaunchCounters>();
@@ -835,7 +838,7 @@ static probesim_status rand_range(probesim_graph *g, Workspace *ws, const QueryB
                                   int32_t *counts, int64_t &launches, cudaStream_t st, bool *too_big) {
     *too_big = false;
     const int32_t W = w1 - w0;
-    const DeviceGraph &dg = g->dg;
+    const DeviceGraph &dg = ws->dg;
     const int32_t L = g->cfg.l_max;
     PS_ALLOC_RANGE(ws->r_cnt.ensure(sizeof(long long) * std::max(1, W)));
     PS_ALLOC_RANGE(ws->r_off.ensure(sizeof(long long) * (W + 1)));
@@ -934,7 +937,7 @@ static probesim_status rand_range(probesim_graph *g, Workspace *ws, const QueryB
 static probesim_status rand_instances(probesim_graph *g, Workspace *ws, const QueryBatch &qb, int32_t B, int32_t W,
                                       int32_t max_len, const int32_t *walk_slot, const uint8_t *t_sw, int64_t &launches,
                                       cudaStream_t st, bool *too_big) {
-    const size_t cn = (size_t)B * g->dg.n;
+    const size_t cn = (size_t)B * g->n;
     PS_ALLOC(ws->r_counts.ensure(sizeof(int32_t) * cn));
     PS_CUDA(cudaMemsetAsync(ws->r_counts.p, 0, sizeof(int32_t) * cn, st));
     bool oom = false;
@@ -982,7 +985,7 @@ static probesim_status run_batch_rand(probesim_graph *g, Workspace *ws, const pr
     int32_t max_len = 0;
     PS_TRY(batch_walks(g, ws, P, qb, &walk_nodes, &max_len, launches, st));
     PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, nullptr, nullptr, launches, st, too_big));
-    launch_rand_finalize(g->dg.n, B, qb.node, ws->r_counts.as<int32_t>(), qb.inv_nr, g->dg.ext2int, g->cfg.shift, d_out,
+    launch_rand_finalize(g->n, B, qb.node, ws->r_counts.as<int32_t>(), qb.inv_nr, ws->dg.ext2int, g->cfg.shift, d_out,
                          st);
     ++launches;
     PS_CUDA(cudaGetLastError());
@@ -996,7 +999,7 @@ static probesim_status run_batch_rand(probesim_graph *g, Workspace *ws, const pr
 static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t B,
                                           float *d_out, cudaStream_t st, bool *too_big) {
     *too_big = false;
-    const DeviceGraph &dg = g->dg;
+    const DeviceGraph &dg = ws->dg;
     const int32_t n = dg.n, L = g->cfg.l_max;
     const bool sw_mode = g->cfg.probe_mode == PROBESIM_PROBE_SWITCH;
     BatchPlan P;
@@ -1308,7 +1311,7 @@ static probesim_status run_queries(probesim_graph *g, Workspace *ws, const probe
     while (done < nq) {
         const int32_t B = std::min(chunk, nq - done);
         bool too_big = false;
-        float *out = d_out + (int64_t)done * g->dg.n;
+        float *out = d_out + (int64_t)done * g->n;
         probesim_status s;
         if (g->cfg.probe_mode == PROBESIM_PROBE_RANDOMIZED)
             s = run_batch_rand(g, ws, q + done, B, out, st, &too_big);
@@ -1335,7 +1338,7 @@ probesim_status ps::check_queries(const probesim_graph *g, const probesim_query 
     if (!q || nq <= 0) return fail(PROBESIM_E_INVALID, "queries: null pointer or nq <= 0");
     if (nq > 65535) return fail(PROBESIM_E_INVALID, "at most 65535 queries per call");
     for (int32_t i = 0; i < nq; ++i) {
-        if (q[i].node < 0 || q[i].node >= g->dg.n) return fail(PROBESIM_E_RANGE, "query node outside [0, n)");
+        if (q[i].node < 0 || q[i].node >= g->n) return fail(PROBESIM_E_RANGE, "query node outside [0, n)");
         if (!(q[i].eps > 0.0 && q[i].eps < 1.0)) return fail(PROBESIM_E_INVALID, "query eps must lie in (0, 1)");
         if (topk && (q[i].k < 1 || q[i].k > kmax)) return fail(PROBESIM_E_INVALID, "query k must lie in [1, kmax]");
     }
@@ -1445,9 +1448,9 @@ probesim_status probesim_pair_mc(probesim_graph *g, const int32_t *u, const int3
     if (npairs < 1 || npairs > 65535) return fail(PROBESIM_E_INVALID, "npairs must lie in [1, 65535]");
     if (r < 1 || r >= ((int64_t)1 << 32)) return fail(PROBESIM_E_INVALID, "r must lie in [1, 2^32)");
     for (int32_t i = 0; i < npairs; ++i)
-        if (u[i] < 0 || u[i] >= g->dg.n || v[i] < 0 || v[i] >= g->dg.n) return fail(PROBESIM_E_RANGE, "node outside [0, n)");
+        if (u[i] < 0 || u[i] >= g->n || v[i] < 0 || v[i] >= g->n) return fail(PROBESIM_E_RANGE, "node outside [0, n)");
     std::lock_guard<std::mutex> lk(g->mu);
-    std::shared_lock<std::shared_mutex> sl(g->store_mu);
+    const std::shared_ptr<StoreVersion> snap = g->current();
     g_last_error.clear();
     Workspace *ws = &g->ws0;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1464,7 +1467,7 @@ probesim_status probesim_pair_mc(probesim_graph *g, const int32_t *u, const int3
     PS_CUDA(cudaMemcpyAsync(d, h, sizeof(int32_t) * words, cudaMemcpyHostToDevice, st));
     unsigned long long *dm = ws->pm_meets.as<unsigned long long>();
     PS_CUDA(cudaMemsetAsync(dm, 0, sizeof(unsigned long long) * npairs, st));
-    launch_pair_mc(g->dg, d, d + npairs, reinterpret_cast<const uint32_t *>(d + 2 * npairs),
+    launch_pair_mc(snap->dg, d, d + npairs, reinterpret_cast<const uint32_t *>(d + 2 * npairs),
                    reinterpret_cast<const uint32_t *>(d + 3 * npairs), npairs, r, g->cfg.l_max, g->cfg.seed, g->t_stop,
                    dm, st);
     PS_CUDA(cudaGetLastError());
@@ -1493,8 +1496,8 @@ probesim_status probesim_set_memory_budget(probesim_graph *g, double bytes) {
 
 probesim_status probesim_graph_destroy(probesim_graph *g) {
     if (!g) return PROBESIM_OK;
-    DevBuf *bufs[] = {&g->in_off, &g->in_col, &g->out_off, &g->out_col, &g->w, &g->piece_v, &g->piece_beg,
-                      &g->piece_len, &g->split_v, &g->ext2int, &g->int2ext, &g->u_batch, &g->u_valid,
+    g->store.reset();
+    DevBuf *bufs[] = {&g->ext2int, &g->int2ext, &g->u_batch, &g->u_valid,
                       &g->u_vpre, &g->u_delta, &g->u_deg, &g->u_part, &g->u_hist};
     for (DevBuf *b : bufs) b->release();
     g->ws0.release();
@@ -1504,9 +1507,10 @@ probesim_status probesim_graph_destroy(probesim_graph *g) {
 
 probesim_status probesim_graph_info(const probesim_graph *g, int32_t *n, int64_t *m, uint64_t *epoch) {
     if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
-    if (n) *n = g->dg.n;
-    if (m) *m = g->dg.m;
-    if (epoch) *epoch = g->epoch;
+    const std::shared_ptr<StoreVersion> v = const_cast<probesim_graph *>(g)->current();
+    if (n) *n = g->n;
+    if (m) *m = v->dg.m;
+    if (epoch) *epoch = v->epoch;
     return PROBESIM_OK;
 }
 
@@ -1516,12 +1520,13 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
                                   int64_t *applied, cudaStream_t st) {
     if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
     if (k < 0 || (k > 0 && (!src || !dst))) return fail(PROBESIM_E_INVALID, "bad update batch");
-    std::unique_lock<std::shared_mutex> lk(g->store_mu);
+    std::lock_guard<std::mutex> lk(g->update_mu);
     g_last_error.clear();
     std::vector<int32_t> hs, hd;
     PS_TRY(fetch_ids(src, k, hs));
     PS_TRY(fetch_ids(dst, k, hd));
-    const int32_t n = g->dg.n;
+    const int32_t n = g->n;
+    const std::shared_ptr<StoreVersion> old = g->current();  // read only; queries may be reading it too
     for (int64_t e = 0; e < k; ++e)
         if (hs[e] < 0 || hs[e] >= n || hd[e] < 0 || hd[e] >= n) return fail(PROBESIM_E_RANGE, "edge id outside [0, n)");
     // the batch without loops and repeats, in the two row orders
@@ -1534,8 +1539,12 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
     std::sort(in_keys.begin(), in_keys.end());
     in_keys.erase(std::unique(in_keys.begin(), in_keys.end()), in_keys.end());
     const int64_t K = (int64_t)in_keys.size();
-    if (K == 0) {
-        g->epoch += 1;
+    if (K == 0) {  // nothing changes but the epoch: the next version shares the current one's arrays
+        auto nv = std::make_shared<StoreVersion>();
+        nv->base = old;
+        nv->dg = old->dg;
+        nv->epoch = old->epoch + 1;
+        g->publish(nv);
         if (applied) *applied = 0;
         return PROBESIM_OK;
     }
@@ -1556,7 +1565,8 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
         out_src[e] = (int32_t)(out_keys[e] >> 32);
         out_dst[e] = (int32_t)(out_keys[e] & 0xffffffffu);
     }
-    DeviceGraph &dg = g->dg;
+    const DeviceGraph &dg = old->dg;
+    auto nv = std::make_shared<StoreVersion>();  // the next version, built beside the current one
     PS_CUDA(g->u_batch.ensure(sizeof(int32_t) * 5 * K));
     PS_CUDA(g->u_valid.ensure(sizeof(long long) * 2 * K));
     PS_CUDA(g->u_vpre.ensure(sizeof(long long) * 2 * (K + 1)));
@@ -1582,7 +1592,7 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
     launch_scan64(a.out_valid, K, g->u_part.as<long long>(), out_vpre, st);
     // new offsets
     long long *deg = g->u_deg.as<long long>(), *deg_out = deg + (n + 1);
-    DevBuf n_in_off, n_out_off, n_in_col, n_out_col;
+    DevBuf &n_in_off = nv->in_off, &n_out_off = nv->out_off, &n_in_col = nv->in_col, &n_out_col = nv->out_col;
     PS_CUDA(n_in_off.ensure(sizeof(int64_t) * ((size_t)n + 1)));
     PS_CUDA(n_out_off.ensure(sizeof(int64_t) * ((size_t)n + 1)));
     launch_upd_degrees(n, dg.in_off, in_delta, deg, st);
@@ -1603,12 +1613,13 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
     launch_upd_rows(dg, a, false, n_out_off.as<long long>(), n_out_col.as<int32_t>(), st);
     // w and pieces of the new in-lists
     const int64_t cap_pieces = (int64_t)n + m2 / kPiece + 1;
-    DevBuf n_pv, n_pb, n_pl, n_split;
+    DevBuf &n_pv = nv->piece_v, &n_pb = nv->piece_beg, &n_pl = nv->piece_len, &n_split = nv->split_v;
     PS_CUDA(n_pv.ensure(sizeof(int32_t) * cap_pieces));
     PS_CUDA(n_pb.ensure(sizeof(int64_t) * cap_pieces));
     PS_CUDA(n_pl.ensure(sizeof(int32_t) * cap_pieces));
     PS_CUDA(n_split.ensure(sizeof(int32_t) * (size_t)n));
-    launch_upd_w(n, n_in_off.as<long long>(), (float)std::sqrt(g->cfg.c), dg.w, deg, st);
+    PS_CUDA(nv->w.ensure(sizeof(float) * (size_t)n));
+    launch_upd_w(n, n_in_off.as<long long>(), (float)std::sqrt(g->cfg.c), nv->w.as<float>(), deg, st);
     unsigned long long *hist = g->u_hist.as<unsigned long long>(), *cursor = hist + (kPiece + 1),
                        *nsplit = cursor + (kPiece + 1);
     launch_upd_pieces(n, n_in_off.as<long long>(), hist, cursor, n_split.as<int32_t>(), nsplit, n_pv.as<int32_t>(),
@@ -1620,28 +1631,23 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
     PS_CUDA(cudaStreamSynchronize(st));
     int64_t npieces = 0;
     for (int len = 0; len <= kPiece; ++len) npieces += (int64_t)hh[len];
-    // swap in the new store
-    std::swap(g->in_off, n_in_off);
-    std::swap(g->out_off, n_out_off);
-    std::swap(g->in_col, n_in_col);
-    std::swap(g->out_col, n_out_col);
-    std::swap(g->piece_v, n_pv);
-    std::swap(g->piece_beg, n_pb);
-    std::swap(g->piece_len, n_pl);
-    std::swap(g->split_v, n_split);
-    for (DevBuf *b : {&n_in_off, &n_out_off, &n_in_col, &n_out_col, &n_pv, &n_pb, &n_pl, &n_split}) b->release();
-    dg.m = m2;
-    dg.in_off = g->in_off.as<int64_t>();
-    dg.out_off = g->out_off.as<int64_t>();
-    dg.in_col = g->in_col.as<int32_t>();
-    dg.out_col = g->out_col.as<int32_t>();
-    dg.n_pieces = npieces;
-    dg.piece_v = g->piece_v.as<int32_t>();
-    dg.piece_beg = g->piece_beg.as<int64_t>();
-    dg.piece_len = g->piece_len.as<int32_t>();
-    dg.n_split = (int32_t)hh[kPiece + 1];
-    dg.split_v = g->split_v.as<int32_t>();
-    g->epoch += 1;
+    // publish the new version: queries that start from now on read it, those in flight keep the old one
+    DeviceGraph &ng = nv->dg;
+    ng = dg;
+    ng.m = m2;
+    ng.in_off = nv->in_off.as<int64_t>();
+    ng.out_off = nv->out_off.as<int64_t>();
+    ng.in_col = nv->in_col.as<int32_t>();
+    ng.out_col = nv->out_col.as<int32_t>();
+    ng.w = nv->w.as<float>();
+    ng.n_pieces = npieces;
+    ng.piece_v = nv->piece_v.as<int32_t>();
+    ng.piece_beg = nv->piece_beg.as<int64_t>();
+    ng.piece_len = nv->piece_len.as<int32_t>();
+    ng.n_split = (int32_t)hh[kPiece + 1];
+    ng.split_v = nv->split_v.as<int32_t>();
+    nv->epoch = old->epoch + 1;
+    g->publish(nv);
     if (applied) *applied = hm[2];
     return PROBESIM_OK;
 }
@@ -1661,7 +1667,7 @@ probesim_status probesim_delete_edges(probesim_graph *g, const int32_t *src, con
 probesim_status probesim_num_walks(const probesim_graph *g, double eps, int64_t *n_r) {
     if (!g || !n_r) return fail(PROBESIM_E_INVALID, "null argument");
     if (!(eps > 0.0 && eps < 1.0)) return fail(PROBESIM_E_INVALID, "eps must lie in (0, 1)");
-    *n_r = num_walks(g->cfg.c, eps, g->cfg.delta, g->dg.n);
+    *n_r = num_walks(g->cfg.c, eps, g->cfg.delta, g->n);
     return PROBESIM_OK;
 }
 
@@ -1670,7 +1676,7 @@ probesim_status probesim_sample_walks(probesim_graph *g, const probesim_query *q
     if (!g || !nodes || !lens) return fail(PROBESIM_E_INVALID, "null argument");
     PS_TRY(check_queries(g, q, nq, false, 0));
     std::lock_guard<std::mutex> lk(g->mu);
-    std::shared_lock<std::shared_mutex> sl(g->store_mu);
+    const std::shared_ptr<StoreVersion> snap = g->current();
     g_last_error.clear();
     Workspace *ws = &g->ws0;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1687,8 +1693,8 @@ probesim_status probesim_sample_walks(probesim_graph *g, const probesim_query *q
     PS_CUDA(cudaMemsetAsync(ws->ctr.p, 0, sizeof(LaunchCounters), st));
     int32_t *wd = dev_nodes ? nodes : ws->walks.as<int32_t>();
     int32_t *ld = dev_lens ? lens : ws->lens.as<int32_t>();
-    launch_walks(g->dg, qb, P.W, L, g->t_stop, g->cfg.seed, wd, ld, true, ws->ctr.as<LaunchCounters>(), st);
-    ps::launch_map_ids(wd, (int64_t)P.W * L, g->dg.int2ext, st);
+    launch_walks(snap->dg, qb, P.W, L, g->t_stop, g->cfg.seed, wd, ld, true, ws->ctr.as<LaunchCounters>(), st);
+    ps::launch_map_ids(wd, (int64_t)P.W * L, snap->dg.int2ext, st);
     PS_CUDA(cudaGetLastError());
     if (!dev_nodes)
         PS_CUDA(cudaMemcpyAsync(nodes, wd, sizeof(int32_t) * (size_t)P.W * L, cudaMemcpyDeviceToHost, st));
@@ -1701,12 +1707,18 @@ probesim_status probesim_sample_walks(probesim_graph *g, const probesim_query *q
 
 // Single-source estimates of nq queries into `scores` (host or device) using workspace ws.  The caller holds
 // the store lock (shared) and owns ws.
-probesim_status ps::single_source_core(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t nq,
-                                          float *scores, cudaStream_t st) {
+probesim_status ps::single_source_core(probesim_graph *g, Workspace *ws, const std::shared_ptr<StoreVersion> &snap,
+                                          const probesim_query *q, int32_t nq, float *scores, cudaStream_t st) {
     ws->stats = probesim_stats{};
+    ws->snap = snap;
+    ws->dg = snap->dg;
+    struct Release {
+        Workspace *w;
+        ~Release() { w->snap.reset(); }
+    } release{ws};
     const bool dev = is_device_ptr(scores);
     float *d_out = scores;
-    const size_t out_bytes = sizeof(float) * (size_t)nq * g->dg.n;
+    const size_t out_bytes = sizeof(float) * (size_t)nq * g->n;
     if (!dev) {
         PS_CUDA(ws->out_stage.ensure(out_bytes));
         d_out = ws->out_stage.as<float>();
@@ -1720,10 +1732,17 @@ probesim_status ps::single_source_core(probesim_graph *g, Workspace *ws, const p
 }
 
 // Top-k of nq queries (ids/vals host or device, [nq][kmax]) using workspace ws; same locking as above.
-probesim_status ps::topk_core(probesim_graph *g, Workspace *ws, const probesim_query *q, int32_t nq, int32_t kmax,
-                                 int32_t *ids, float *vals, cudaStream_t st) {
+probesim_status ps::topk_core(probesim_graph *g, Workspace *ws, const std::shared_ptr<StoreVersion> &snap,
+                                 const probesim_query *q, int32_t nq, int32_t kmax, int32_t *ids, float *vals,
+                                 cudaStream_t st) {
     ws->stats = probesim_stats{};
-    const int32_t n = g->dg.n;
+    ws->snap = snap;
+    ws->dg = snap->dg;
+    struct Release {
+        Workspace *w;
+        ~Release() { w->snap.reset(); }
+    } release{ws};
+    const int32_t n = g->n;
     // scores of a chunk of queries, then the selection
     const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(g->budget / 8) / ((int64_t)n * 4)));
     PS_CUDA(ws->out_stage.ensure(sizeof(float) * (size_t)chunk * n));
@@ -1776,20 +1795,18 @@ probesim_status probesim_single_source(probesim_graph *g, const probesim_query *
     if (!g || !scores) return fail(PROBESIM_E_INVALID, "null argument");
     PS_TRY(check_queries(g, q, nq, false, 0));
     std::lock_guard<std::mutex> lk(g->mu);
-    std::shared_lock<std::shared_mutex> sl(g->store_mu);
     g_last_error.clear();
-    return single_source_core(g, &g->ws0, q, nq, scores, (cudaStream_t)stream);
+    return single_source_core(g, &g->ws0, g->current(), q, nq, scores, (cudaStream_t)stream);
 }
 
 probesim_status probesim_topk(probesim_graph *g, const probesim_query *q, int32_t nq, int32_t kmax, int32_t *ids,
                               float *vals, void *stream) {
     if (!g || !ids || !vals) return fail(PROBESIM_E_INVALID, "null argument");
-    if (kmax < 1 || kmax > 4096 || kmax > g->dg.n - 1) return fail(PROBESIM_E_INVALID, "kmax must lie in [1, min(4096, n-1)]");
+    if (kmax < 1 || kmax > 4096 || kmax > g->n - 1) return fail(PROBESIM_E_INVALID, "kmax must lie in [1, min(4096, n-1)]");
     PS_TRY(check_queries(g, q, nq, true, kmax));
     std::lock_guard<std::mutex> lk(g->mu);
-    std::shared_lock<std::shared_mutex> sl(g->store_mu);
     g_last_error.clear();
-    return topk_core(g, &g->ws0, q, nq, kmax, ids, vals, (cudaStream_t)stream);
+    return topk_core(g, &g->ws0, g->current(), q, nq, kmax, ids, vals, (cudaStream_t)stream);
 }
 
 // Times the pull on this graph's in-lists for every tile width in {1, 2, 4, 8, 16, 32} and blocks-per-SM in
@@ -1798,10 +1815,10 @@ probesim_status probesim_topk(probesim_graph *g, const probesim_query *q, int32_
 probesim_status probesim_autotune(probesim_graph *g, void *stream) {
     if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
     std::lock_guard<std::mutex> lk(g->mu);
-    std::shared_lock<std::shared_mutex> sl(g->store_mu);
+    const std::shared_ptr<StoreVersion> snap = g->current();
     g_last_error.clear();
     cudaStream_t st = (cudaStream_t)stream;
-    const DeviceGraph &dg = g->dg;
+    const DeviceGraph &dg = snap->dg;
     const int32_t n = dg.n, P = 64;
     Workspace *ws = &g->ws0;
     PS_CUDA(ws->md_a.ensure((size_t)(n + 1) * P * sizeof(float)));  // a spare row after the n rows

@@ -5,8 +5,9 @@
 // max_batch queries, admitted while the estimated score-buffer memory of the batches in flight stays within
 // the budget.  Requests that arrive while other batches run are admitted by the next free worker, so batches
 // of different workers overlap on the device.  An update batch at the head of the FIFO is applied between
-// batches: the worker takes the store exclusively (it waits for in-flight batches) and every query behind it
-// sees the new edge set.  Each result records the epoch it saw and its submit-to-completion latency.
+// batches: the worker builds the next store version beside the current one and publishes it -- batches in
+// flight keep reading the version they started with -- and every query behind it sees the new edge set.  Each
+// result records the epoch it saw and its submit-to-completion latency.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -63,7 +64,7 @@ struct probesim_server {
 // Score-buffer bytes a query needs at its widest depth: about 0.25 n_r vectors of n FP32 in three buffers.
 static double query_bytes(const probesim_server *s, const probesim_query &q) {
     const double nr = (double)ps::num_walks_for(s->g, q.eps);
-    return 3.0 * 4.0 * (double)s->g->dg.n * std::max(1.0, 0.25 * nr);
+    return 3.0 * 4.0 * (double)s->g->n * std::max(1.0, 0.25 * nr);
 }
 
 static void worker_loop(probesim_server *s, int wid) {
@@ -80,9 +81,9 @@ static void worker_loop(probesim_server *s, int wid) {
         Request update;
         bool have_update = false;
         double mem = 0.0;
-        // a batch takes the store (shared) before the queue lock is released, so an update batch behind it in
-        // the FIFO cannot be applied before the batch has read the store
-        std::shared_lock<std::shared_mutex> store(s->g->store_mu, std::defer_lock);
+        // a batch takes its store version before the queue lock is released, so an update batch behind it in the
+        // FIFO cannot change what it reads; the update builds the next version beside it
+        std::shared_ptr<StoreVersion> snap;
         uint64_t epoch = 0;
         {
             std::unique_lock<std::mutex> lk(s->mu);
@@ -109,11 +110,11 @@ static void worker_loop(probesim_server *s, int wid) {
                 s->queued_queries -= (int64_t)batch.size();
                 s->mem_in_flight += mem;
                 s->batches_in_flight += 1;
-                store.lock();
-                epoch = s->g->epoch;
+                snap = s->g->current();
+                epoch = snap->epoch;
             }
         }
-        if (have_update) {  // epoch boundary: exclusive access to the store
+        if (have_update) {  // epoch boundary: queries behind it wait (admissions held), those in flight do not
             int64_t applied = 0;
             probesim_status rc = ps::apply_updates(s->g, update.src.data(), update.dst.data(), (int64_t)update.src.size(),
                                                    update.insert, &applied, st);
@@ -129,8 +130,8 @@ static void worker_loop(probesim_server *s, int wid) {
         const int32_t B = (int32_t)batch.size();
         ids.assign((size_t)B * kmax, -1);
         vals.assign((size_t)B * kmax, 0.f);
-        const probesim_status rc = ps::topk_core(s->g, ws, qs.data(), B, kmax, ids.data(), vals.data(), st);
-        store.unlock();
+        const probesim_status rc = ps::topk_core(s->g, ws, snap, qs.data(), B, kmax, ids.data(), vals.data(), st);
+        snap.reset();
         const Clock::time_point t_end = Clock::now();
         {
             std::lock_guard<std::mutex> lk(s->mu);
@@ -185,7 +186,7 @@ probesim_status probesim_server_create(probesim_graph *g, const probesim_server_
     if (cfg) c = *cfg; else probesim_server_config_default(&c);
     if (c.workers < 1 || c.workers > 8) return ps::fail_status(PROBESIM_E_INVALID, "workers must lie in [1, 8]");
     if (c.max_batch < 1 || c.max_batch > 4096) return ps::fail_status(PROBESIM_E_INVALID, "max_batch must lie in [1, 4096]");
-    if (c.kmax < 1 || c.kmax > 4096 || c.kmax > g->dg.n - 1)
+    if (c.kmax < 1 || c.kmax > 4096 || c.kmax > g->n - 1)
         return ps::fail_status(PROBESIM_E_INVALID, "kmax must lie in [1, min(4096, n-1)]");
     if (c.queue_capacity < 1) return ps::fail_status(PROBESIM_E_INVALID, "queue_capacity must be >= 1");
     if (!(c.memory_budget_bytes >= 0.0)) return ps::fail_status(PROBESIM_E_INVALID, "memory_budget_bytes must be >= 0");
@@ -246,7 +247,7 @@ probesim_status probesim_server_submit(probesim_server *s, const probesim_query 
 probesim_status probesim_server_update(probesim_server *s, const int32_t *src, const int32_t *dst, int64_t k,
                                        int32_t insert) {
     if (!s || k < 0 || (k > 0 && (!src || !dst))) return ps::fail_status(PROBESIM_E_INVALID, "bad update batch");
-    const int32_t n = s->g->dg.n;
+    const int32_t n = s->g->n;
     Request r;
     r.is_update = true;
     r.insert = insert != 0;

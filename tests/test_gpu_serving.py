@@ -107,3 +107,38 @@ def test_full_queue_is_refused(graph):
             refused += 1
     assert refused > 0 and S.stats()["rejected"] == refused
     S.close()
+
+
+def test_update_does_not_wait_for_a_query_in_flight():
+    """An update batch builds the next store version beside the current one: applied from another thread while a
+    long query runs, it returns before the query ends, and the query's estimates are those of the graph it
+    started on (the store version it holds)."""
+    import threading
+    from paper_1709_06955_gb300 import probesim
+    n, s, d = synth.rmat(16, 16 << 16, seed=16)
+    G = probesim.Graph(n, s, d)
+    qs = synth.queries(n, d, 8, seed=161)
+    Q = probesim.make_queries(qs, eps=0.03, query_ids=np.arange(8) + 90)
+    ref_old = probesim.Graph(n, s, d).single_source(Q)
+    G.single_source(probesim.make_queries(qs[:1], eps=0.2, query_ids=[1]))  # warm up the workspace
+    box = {}
+
+    def run():
+        box["t0"] = time.perf_counter()
+        box["out"] = G.single_source(Q)
+        box["t1"] = time.perf_counter()
+
+    th = threading.Thread(target=run)
+    th.start()
+    time.sleep(0.2)
+    rng = np.random.default_rng(4)
+    t_upd0 = time.perf_counter()
+    applied = G.insert_edges(rng.integers(0, n, 20000).astype(np.int32), rng.integers(0, n, 20000).astype(np.int32))
+    t_upd1 = time.perf_counter()
+    th.join()
+    assert applied > 0 and G.info()[2] == 1
+    assert t_upd1 < box["t1"], "the update waited for the query"  # it returned while the query still ran
+    assert np.max(np.abs(box["out"] - ref_old)) <= TOL
+    new = G.single_source(Q)  # a query that starts after the update sees it
+    assert np.max(np.abs(new - ref_old)) > 1e-3
+    del t_upd0
