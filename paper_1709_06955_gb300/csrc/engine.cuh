@@ -19,6 +19,21 @@
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+    bool pooled = false;  // from the stream-ordered pool (cudaMallocAsync): freed with cudaFreeAsync
+    // allocates exactly `bytes` from the device's stream-ordered pool on stream s (no device-wide synchronisation,
+    // unlike cudaMalloc / cudaFree); for buffers that are written once, such as a new version of the graph store
+    cudaError_t alloc_pooled(size_t bytes, cudaStream_t s) {
+        release();
+        cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(256, bytes), s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return e;
+        }
+        cap = std::max<size_t>(256, bytes);
+        pooled = true;
+        return cudaSuccess;
+    }
     cudaError_t ensure(size_t bytes) {
         if (bytes <= cap && p) return cudaSuccess;
         if (p) cudaFree(p);
@@ -46,10 +61,16 @@ struct DevBuf {
         cap = nb;
         return e;
     }
+    // A pooled buffer returns to the pool on the calling thread's default stream, without waiting: its readers
+    // have synchronised their own streams before they let go of it.
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (pooled) cudaFreeAsync(p, cudaStreamPerThread);
+            else cudaFree(p);
+        }
         p = nullptr;
         cap = 0;
+        pooled = false;
     }
     template <class T>
     T *as() const { return static_cast<T *>(p); }

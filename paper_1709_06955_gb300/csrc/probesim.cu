@@ -1437,6 +1437,22 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
         return s;
     }
     std::vector<uint64_t>().swap(g->keys);  // later updates merge on the device
+    {   // update batches allocate store versions from the device's stream-ordered pool: let it keep about three
+        // versions' worth of memory between updates instead of returning it to the driver at every synchronisation
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, g->device) == cudaSuccess) {
+            const std::shared_ptr<StoreVersion> v = g->current();
+            uint64_t keep = 0;
+            for (DevBuf *b : {&v->in_off, &v->in_col, &v->out_off, &v->out_col, &v->w, &v->piece_v, &v->piece_beg,
+                              &v->piece_len, &v->split_v})
+                keep += b->cap;
+            keep *= 3;
+            uint64_t cur = 0;
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur);
+            if (cur < keep) cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     *out = g;
     return PROBESIM_OK;
 }
@@ -1593,8 +1609,8 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
     // new offsets
     long long *deg = g->u_deg.as<long long>(), *deg_out = deg + (n + 1);
     DevBuf &n_in_off = nv->in_off, &n_out_off = nv->out_off, &n_in_col = nv->in_col, &n_out_col = nv->out_col;
-    PS_CUDA(n_in_off.ensure(sizeof(int64_t) * ((size_t)n + 1)));
-    PS_CUDA(n_out_off.ensure(sizeof(int64_t) * ((size_t)n + 1)));
+    PS_CUDA(n_in_off.alloc_pooled(sizeof(int64_t) * ((size_t)n + 1), st));
+    PS_CUDA(n_out_off.alloc_pooled(sizeof(int64_t) * ((size_t)n + 1), st));
     launch_upd_degrees(n, dg.in_off, in_delta, deg, st);
     launch_scan64(deg, n, g->u_part.as<long long>(), n_in_off.as<long long>(), st);
     launch_upd_degrees(n, dg.out_off, out_delta, deg_out, st);
@@ -1607,18 +1623,18 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
     const int64_t m2 = hm[0];
     if (m2 != hm[1]) return fail(PROBESIM_E_CUDA, "internal: in- and out-lists disagree after the update");
     if (m2 >= ((int64_t)1 << 31)) return fail(PROBESIM_E_INVALID, "edge count would reach 2^31");
-    PS_CUDA(n_in_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m2)));
-    PS_CUDA(n_out_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m2)));
+    PS_CUDA(n_in_col.alloc_pooled(sizeof(int32_t) * std::max<int64_t>(1, m2), st));
+    PS_CUDA(n_out_col.alloc_pooled(sizeof(int32_t) * std::max<int64_t>(1, m2), st));
     launch_upd_rows(dg, a, true, n_in_off.as<long long>(), n_in_col.as<int32_t>(), st);
     launch_upd_rows(dg, a, false, n_out_off.as<long long>(), n_out_col.as<int32_t>(), st);
     // w and pieces of the new in-lists
     const int64_t cap_pieces = (int64_t)n + m2 / kPiece + 1;
     DevBuf &n_pv = nv->piece_v, &n_pb = nv->piece_beg, &n_pl = nv->piece_len, &n_split = nv->split_v;
-    PS_CUDA(n_pv.ensure(sizeof(int32_t) * cap_pieces));
-    PS_CUDA(n_pb.ensure(sizeof(int64_t) * cap_pieces));
-    PS_CUDA(n_pl.ensure(sizeof(int32_t) * cap_pieces));
-    PS_CUDA(n_split.ensure(sizeof(int32_t) * (size_t)n));
-    PS_CUDA(nv->w.ensure(sizeof(float) * (size_t)n));
+    PS_CUDA(n_pv.alloc_pooled(sizeof(int32_t) * cap_pieces, st));
+    PS_CUDA(n_pb.alloc_pooled(sizeof(int64_t) * cap_pieces, st));
+    PS_CUDA(n_pl.alloc_pooled(sizeof(int32_t) * cap_pieces, st));
+    PS_CUDA(n_split.alloc_pooled(sizeof(int32_t) * (size_t)n, st));
+    PS_CUDA(nv->w.alloc_pooled(sizeof(float) * (size_t)n, st));
     launch_upd_w(n, n_in_off.as<long long>(), (float)std::sqrt(g->cfg.c), nv->w.as<float>(), deg, st);
     unsigned long long *hist = g->u_hist.as<unsigned long long>(), *cursor = hist + (kPiece + 1),
                        *nsplit = cursor + (kPiece + 1);
