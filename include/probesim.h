@@ -211,11 +211,14 @@ probesim_status probesim_get_stats(const probesim_graph *g, probesim_stats *out)
 /* ---------------------------------------------------------------------------------------------------------
  * Serving loop (continuous batching).  Queries and edge-update batches enter one FIFO.  `workers` threads,
  * each with its own scratch memory and CUDA stream, take the next batch of queries from the head as soon as
- * they are free: up to max_batch queries, admitted while the estimated score-buffer memory of the batches in
- * flight (about 12 * n * 0.25 * n_r bytes per query) stays within memory_budget_bytes.  Queries that arrive
- * while other batches run are admitted by the next free worker, so the work of several batches overlaps on
- * the device.  An update batch at the head is applied between batches: queries submitted after it see the
- * new edge set, queries submitted before it the old one.  Results are top-k lists (Def. 2).
+ * they are free: up to max_batch queries, admitted while the estimated memory of the batches in flight stays
+ * within memory_budget_bytes (the deterministic engine's score buffers, about 12 * n * 0.25 * n_r bytes per
+ * query; with Pruning Rule 2, the switch or the randomized PROBE, an estimate row and walk rows, 12 n + 8 l_max
+ * n_r bytes, since those engines fit their level tables into each worker's share of the budget, 1/workers of
+ * it).  Queries that arrive while other batches run are admitted by the next free worker, so the work of
+ * several batches overlaps on the device.  An update batch at the head is applied between batches: queries
+ * submitted after it see the new edge set, queries submitted before it the old one; it builds the next store
+ * version while earlier batches still run.  Results are top-k lists (Def. 2).
  * --------------------------------------------------------------------------------------------------------- */
 typedef struct probesim_server probesim_server;
 

@@ -129,6 +129,7 @@ struct Workspace {
     PinnedBuf pin_q;  // query arrays of one batch
     PinnedBuf pin_s;  // counters and schedule offsets (fixed size, allocated at creation)
     int profiling = 0;
+    size_t budget = 0;  // device memory one call on this workspace may take; 0 = the graph's budget
     std::shared_ptr<StoreVersion> snap;  // the store version of the call in progress
     ps::DeviceGraph dg;                  // its device view
     std::vector<cudaEvent_t> ev;

@@ -224,6 +224,11 @@ static probesim_status upload_graph(probesim_graph *g, int32_t n, cudaStream_t s
     return PROBESIM_OK;
 }
 
+// Device memory one call on workspace ws may take (a server gives each worker a share of the graph's budget).
+static size_t budget_of(const probesim_graph *g, const Workspace *ws) {
+    return ws->budget ? ws->budget : g->budget.load();
+}
+
 // Copies an int32 array that may live on the device to the host.
 static probesim_status fetch_ids(const int32_t *p, int64_t k, std::vector<int32_t> &out) {
     out.resize(std::max<int64_t>(1, k));
@@ -354,7 +359,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     const int32_t L = g->cfg.l_max;
     BatchPlan P;
     PS_TRY(plan_batch(g, q, B, P));
-    if ((size_t)P.W * L * 4 > g->budget / 4 && B > 1) {
+    if ((size_t)P.W * L * 4 > budget_of(g, ws) / 4 && B > 1) {
         *too_big = true;
         return PROBESIM_E_NOMEM;
     }
@@ -597,7 +602,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
         for (size_t r = 0; r < pa.size(); ++r) col[pa[r]] = h0v[d] + (int32_t)r;
     }
     const size_t level_bytes2 = 2 * (size_t)max_floats * sizeof(float);
-    if (level_bytes2 > g->budget) {
+    if (level_bytes2 > budget_of(g, ws)) {
         *too_big = B > 1;
         return fail(PROBESIM_E_NOMEM, "score vectors of one query exceed the workspace budget");
     }
@@ -891,7 +896,7 @@ static probesim_status rand_range(probesim_graph *g, Workspace *ws, const QueryB
         if (E <= 0) break;
         const int nx = cur ^ 1;
         const int64_t ncap = next_pow2(std::max<int64_t>(1024, 2 * E));
-        if ((size_t)(8 * ncap + 8 * E) > g->budget / 4 && w1 - w0 > 1) {  // a smaller walk range fits the budget
+        if ((size_t)(8 * ncap + 8 * E) > budget_of(g, ws) / 4 && w1 - w0 > 1) {  // a smaller walk range fits the budget
             *too_big = true;
             return fail(PROBESIM_E_NOMEM, "randomized PROBE level exceeds a quarter of the memory budget");
         }
@@ -1010,7 +1015,7 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
             return fail(PROBESIM_E_INVALID, "eps too small: Pruning Rule 2 and the switch take at most 2^18 walks per query");
         max_w = std::max<int64_t>(max_w, P.base[b + 1] - P.base[b]);
     }
-    if ((size_t)P.W * L * 8 > g->budget / 4 && B > 1) {
+    if ((size_t)P.W * L * 8 > budget_of(g, ws) / 4 && B > 1) {
         *too_big = true;
         return PROBESIM_E_NOMEM;
     }
@@ -1108,8 +1113,8 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     // level whose next frontier might not fit the list budget processes the passes that fit and defers the other
     // probes, with their level-j entries, to a stack; they resume once the processed range has run out.  Every
     // probe's last-level pushes land in the estimate exactly once, whatever the split.
-    const long long pass_slots = std::max<long long>((long long)n, (long long)(g->budget / 4 / 12));
-    const long long list_cap = std::max<long long>((long long)n, (long long)(g->budget / 8 / 12));
+    const long long pass_slots = std::max<long long>((long long)n, (long long)(budget_of(g, ws) / 4 / 12));
+    const long long list_cap = std::max<long long>((long long)n, (long long)(budget_of(g, ws) / 8 / 12));
     auto list_of = [&](int k) {
         FrontierList F;
         F.p = ws->f_lp[k].as<int32_t>();
@@ -1760,7 +1765,7 @@ probesim_status ps::topk_core(probesim_graph *g, Workspace *ws, const std::share
     } release{ws};
     const int32_t n = g->n;
     // scores of a chunk of queries, then the selection
-    const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(g->budget / 8) / ((int64_t)n * 4)));
+    const int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(budget_of(g, ws) / 8) / ((int64_t)n * 4)));
     PS_CUDA(ws->out_stage.ensure(sizeof(float) * (size_t)chunk * n));
     const int nblk = topk_blocks_per_query(n);
     PS_CUDA(ws->tk_hist.ensure(sizeof(unsigned) * 256 * chunk));

@@ -61,10 +61,15 @@ struct probesim_server {
     std::vector<cudaStream_t> streams;
 };
 
-// Score-buffer bytes a query needs at its widest depth: about 0.25 n_r vectors of n FP32 in three buffers.
+// Device bytes a query takes in a batch.  The regrouped deterministic engine holds about 0.25 n_r score vectors
+// of n FP32 in three buffers at its widest depth.  The frontier and randomized engines hold an estimate row
+// (8 + 4 bytes per node) and walk rows of the query's n_r walks (8 bytes per node slot); their level tables and
+// hash sets adapt to the worker's share of the budget (passes, deferred ranges, walk ranges).
 static double query_bytes(const probesim_server *s, const probesim_query &q) {
-    const double nr = (double)ps::num_walks_for(s->g, q.eps);
-    return 3.0 * 4.0 * (double)s->g->n * std::max(1.0, 0.25 * nr);
+    const double nr = (double)ps::num_walks_for(s->g, q.eps), n = (double)s->g->n;
+    const probesim_config &c = s->g->cfg;
+    if (c.probe_mode != PROBESIM_PROBE_DETERMINISTIC || c.eps_p > 0.f) return 12.0 * n + 8.0 * c.l_max * nr;
+    return 3.0 * 4.0 * n * std::max(1.0, 0.25 * nr);
 }
 
 static void worker_loop(probesim_server *s, int wid) {
@@ -206,6 +211,7 @@ probesim_status probesim_server_create(probesim_graph *g, const probesim_server_
             probesim_server_destroy(s);
             return ps::fail_status(PROBESIM_E_NOMEM, "server workspace allocation failed");
         }
+        ws->budget = (size_t)(c.memory_budget_bytes / c.workers);  // the workers' calls share the budget
         s->ws.push_back(ws);
         s->streams.push_back(st);
     }
