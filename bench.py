@@ -14,6 +14,8 @@ timed events).  Also reported, each on its own line of the JSON object:
                with k uniform over {10, 50, 100}, one window with edge-update batches every 100 ms
   serving_2p23 R-MAT 2^23 (m = 2^27), eps uniform over {0.1, 0.05, 0.025}, switch mode, update batches of
                10k edges every 100 ms, Poisson rates bracketing capacity
+  accuracy_pooling  Precision@50, NDCG@50 and Kendall tau of each engine's top-50 lists against a pooled ground
+               truth gauged by the GPU pairwise Monte Carlo (Sec. 6's large-graph protocol)
   e2e          the headline with host output buffers (the scores copied back inside the timed region)
   roofline     the PROBE level kernel's achieved bandwidth against the measured HBM copy peak
   cpu_baseline the FP64 oracle on every host core, on a bounded sample of the headline workload
@@ -68,6 +70,7 @@ def parse():
     ap.add_argument("--serve23-rates", default="2,4,6,8",
                     help="arrival rates of the serving leg on R-MAT 2^23 (empty = off)")
     ap.add_argument("--serve23-seconds", type=float, default=5.0)
+    ap.add_argument("--accuracy-queries", type=int, default=5, help="queries of the pooling accuracy leg (0 = off)")
     return ap.parse_args()
 
 
@@ -411,6 +414,14 @@ def run_ours(args):
         del outb
     best = max(batched, key=lambda r: r["value"]) if batched else None
 
+    # top-50 lists of a few queries from each engine, for the pooling accuracy leg below
+    acc_nodes = [qs[replica_query_id(rank, 7000 + j) % nq] for j in range(args.accuracy_queries)]
+    acc_q = probesim.make_queries(acc_nodes, eps=EPS, k=50,
+                                  query_ids=[replica_query_id(rank, 7000 + j) for j in range(len(acc_nodes))])
+    acc_lists = {}
+    if acc_nodes:
+        acc_lists["deterministic"] = G.topk(acc_q, kmax=50)[0]
+
     # the switch of Sec. 4.4 on the same graph: a few queries one at a time and in calls of 8
     GS = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_SWITCH, c0=args.switch_c0)
     GS.single_source(query(0), out=out, stream=sptr)
@@ -418,10 +429,13 @@ def run_ours(args):
     sw_ms = timed_calls(GS, [query(args.warmup + i) for i in range(sq)], out, stream, flush)
     sst = GS.stats()
     out8 = torch.zeros((8, n), dtype=torch.float32, device=dev)
-    sw8_ms = timed_calls(GS, [qbatch(args.warmup + 8 * i, 8) for i in range(sq // 8)], out8, stream, flush)
+    n8 = max(1, sq // 8)
+    sw8_ms = timed_calls(GS, [qbatch(args.warmup + 8 * i, 8) for i in range(n8)], out8, stream, flush)
     switch = {"c0": args.switch_c0, "eps": EPS, "value": sq / (sum(sw_ms) / 1e3), "unit": "queries/s", "queries": sq,
-              "batched8_value": 8 * (sq // 8) / (sum(sw8_ms) / 1e3),
+              "batched8_value": 8 * n8 / (sum(sw8_ms) / 1e3),
               "last_query": {k: sst[k] for k in ("probes", "switched", "edge_gathers", "levels", "max_table_slots")}}
+    if acc_nodes:
+        acc_lists["switch c0=%g" % args.switch_c0] = GS.topk(acc_q, kmax=50)[0]
     GS.close()
     del out8
 
@@ -431,9 +445,32 @@ def run_ours(args):
     GR.single_source(query(0), out=out, stream=sptr)
     rand_ms = timed_calls(GR, [query(args.warmup + i) for i in range(rq)], out, stream, flush)
     rst = GR.stats()
+    if acc_nodes:
+        acc_lists["randomized"] = GR.topk(acc_q, kmax=50)[0]
     GR.close()
     randomized = {"value": rq / (sum(rand_ms) / 1e3), "unit": "queries/s", "queries": rq,
                   "candidates_last_query": rst["edge_gathers"], "levels_last_query": rst["levels"]}
+
+    # accuracy by pooling (Sec. 6, large graphs): each query's top-50 lists of the three engines are merged, every
+    # pooled node gauged by the GPU pairwise Monte Carlo, and the best 50 taken as the ground truth
+    accuracy = None
+    if acc_nodes:
+        from paper_1709_06955_gb300 import accuracy as A
+        t0 = time.perf_counter()
+        per = {m: [] for m in acc_lists}
+        pool_sizes = []
+        for t, u in enumerate(acc_nodes):
+            truth, score = A.pool(G, int(u), [acc_lists[m][t] for m in acc_lists], 50, eps=2e-4, delta=1e-4,
+                                  key_base=(1 << 30) + 4096 * t)
+            pool_sizes.append(len(score))
+            for m in acc_lists:
+                per[m].append(A.evaluate(acc_lists[m][t], truth, lambda v, sc=score: sc.get(v, 0.0)))
+        accuracy = {"queries": len(acc_nodes), "k": 50, "eps": EPS,
+                    "expert": "pairwise Monte Carlo on the GPU, eps 2e-4, delta 1e-4 (%d walk pairs per node)"
+                              % A.mc_walk_pairs(2e-4, 1e-4),
+                    "mean_pool": float(np.mean(pool_sizes)), "seconds": time.perf_counter() - t0,
+                    "methods": {m: {k: float(np.mean([r[k] for r in per[m]])) for k in ("precision", "ndcg", "tau")}
+                                for m in per}}
 
     # end-to-end through the C ABI with host buffers: query struct in, pinned host scores out
     host_out = torch.empty((1, n), dtype=torch.float32, pin_memory=True)
@@ -551,6 +588,7 @@ def run_ours(args):
             "profiled_ms_per_query": prof["step_ms"] / np_,
             "switch": switch,
             "randomized_probe": randomized,
+            "accuracy_pooling": accuracy,
             "mixed_eps_topk": mixed,
             "serving": serving,
             "serving_2p23": serving23,
