@@ -71,6 +71,9 @@ def parse():
                     help="arrival rates of the serving leg on R-MAT 2^23 (empty = off)")
     ap.add_argument("--serve23-seconds", type=float, default=5.0)
     ap.add_argument("--accuracy-queries", type=int, default=5, help="queries of the pooling accuracy leg (0 = off)")
+    ap.add_argument("--profile-case", choices=["frontier"], default=None,
+                    help="run one small case for an ncu capture and exit (frontier: R-MAT 2^20 drawn on the GPU, "
+                         "switch mode c0 = 0.01, two calls of four queries at eps = 0.1)")
     return ap.parse_args()
 
 
@@ -603,8 +606,29 @@ def run_ours(args):
     return 0
 
 
+def profile_case(args):
+    """A small, fixed invocation of one engine for kernel captures (no timing, no JSON line)."""
+    import numpy as np
+    import torch
+    from paper_1709_06955_gb300 import build, probesim, synth
+    build.build()
+    n, s, d = synth.rmat_device(20, 16 << 20, seed=1)
+    torch.cuda.empty_cache()
+    qs = synth.queries(n, d, 8, seed=2)
+    G = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_SWITCH, c0=0.01)
+    out = torch.zeros((4, n), dtype=torch.float32, device="cuda")
+    for i in range(2):
+        G.single_source(probesim.make_queries(qs[4 * i:4 * i + 4], eps=EPS, query_ids=np.arange(4) + 4 * i), out=out)
+    torch.cuda.synchronize()
+    print("profile case %s done: %d deterministic edge pushes, %d levels" % (args.profile_case, G.stats()["edge_gathers"],
+                                                                          G.stats()["levels"]))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
