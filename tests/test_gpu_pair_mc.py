@@ -63,7 +63,7 @@ def test_pair_mc_estimates_simrank(cl1k):
 
 def test_accuracy_harness_on_gpu(cl1k):
     """Sec. 6's measures of the GPU's top-50 lists (deterministic, switch and randomized PROBE, eps = 0.1) against
-    the Power Method, and the pooling protocol (the pair estimator as the expert) giving the same verdicts."""
+    the Power Method, and the pooling protocol (the pair estimator as the expert) measuring the lists about as the Power Method does."""
     from oracle import power_method
     from paper_1709_06955_gb300 import probesim
     n, s, d = cl1k
@@ -86,7 +86,7 @@ def test_accuracy_harness_on_gpu(cl1k):
         for name in modes:
             r = A.evaluate(lists[name][t], truth, lambda v, u=u: S[u, v], S[u], ests[name][t], u)
             assert r["abs_error"] <= 0.1 and r["precision"] >= 0.8 and r["ndcg"] >= 0.97
-            # pooling can only rank what some method returned: its verdict is close to the exact one
+            # pooling can only rank what some method returned: its precision is close to the exact one
             pr = A.precision_at_k(lists[name][t], ptruth)
             assert abs(pr - r["precision"]) <= 0.12
         # the expert's scores follow the Power Method within its error
