@@ -14,6 +14,8 @@ timed events).  Also reported, each on its own line of the JSON object:
                with k uniform over {10, 50, 100}, one window with edge-update batches every 100 ms
   serving_2p23 R-MAT 2^23 (m = 2^27), eps uniform over {0.1, 0.05, 0.025}, switch mode, update batches of
                10k edges every 100 ms, Poisson rates bracketing capacity
+  billion_edge_topk  R-MAT 2^25 with 10^9 edges, drawn and built on the GPU: top-50 in calls of 64 queries at
+               eps = 0.1, switch mode
   accuracy_pooling  Precision@50, NDCG@50 and Kendall tau of each engine's top-50 lists against a pooled ground
                truth gauged by the GPU pairwise Monte Carlo (Sec. 6's large-graph protocol)
   e2e          the headline with host output buffers (the scores copied back inside the timed region)
@@ -70,6 +72,9 @@ def parse():
     ap.add_argument("--serve23-rates", default="2,4,6,8",
                     help="arrival rates of the serving leg on R-MAT 2^23 (empty = off)")
     ap.add_argument("--serve23-seconds", type=float, default=5.0)
+    ap.add_argument("--billion-batches", type=int, default=2,
+                    help="calls of 64 top-50 queries on R-MAT 2^25 with 10^9 edges (0 = off)")
+    ap.add_argument("--billion-edges", type=float, default=1e9, help="edges of that graph")
     ap.add_argument("--accuracy-queries", type=int, default=5, help="queries of the pooling accuracy leg (0 = off)")
     ap.add_argument("--profile-case", choices=["frontier"], default=None,
                     help="run one small case for an ncu capture and exit (frontier: R-MAT 2^20 drawn on the GPU, "
@@ -439,6 +444,10 @@ def run_ours(args):
               "last_query": {k: sst[k] for k in ("probes", "switched", "edge_gathers", "levels", "max_table_slots")}}
     if acc_nodes:
         acc_lists["switch c0=%g" % args.switch_c0] = GS.topk(acc_q, kmax=50)[0]
+        # the same queries at eps / 4 (16 times the walks): how far the lists' order is set by the estimates' noise
+        acc_fine = probesim.make_queries(acc_nodes, eps=EPS / 4, k=50,
+                                         query_ids=[replica_query_id(rank, 7000 + j) for j in range(len(acc_nodes))])
+        acc_lists["switch c0=%g eps=%g" % (args.switch_c0, EPS / 4)] = GS.topk(acc_fine, kmax=50)[0]
     GS.close()
     del out8
 
@@ -551,6 +560,51 @@ def run_ours(args):
         del s23h, d23h
         torch.cuda.empty_cache()
 
+    # R-MAT 2^25 with 10^9 edges, built on the device: top-50 in calls of 64 queries at eps 0.1, switch mode (the
+    # randomized PROBE takes the high-degree frontiers)
+    billion = None
+    if args.billion_batches > 0:
+        t0 = time.perf_counter()
+        n25, s25, d25 = synth.rmat_device(25, int(args.billion_edges), seed=1, device=dev)
+        torch.cuda.synchronize(dev)
+        gen_s = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+        BB = 64
+        q25 = synth.queries(n25, d25, BB * args.billion_batches, seed=2)
+        t0 = time.perf_counter()
+        G25 = probesim.Graph(n25, s25, d25, probe_mode=probesim.PROBE_SWITCH, c0=args.switch_c0)
+        torch.cuda.synchronize(dev)
+        create_s = time.perf_counter() - t0
+        m25 = G25.info()[1]
+        del s25, d25
+        torch.cuda.empty_cache()
+        bids = torch.empty((BB, 50), dtype=torch.int32, device=dev)
+        bvals = torch.empty((BB, 50), dtype=torch.float32, device=dev)
+        G25.topk(probesim.make_queries(q25[:4], eps=EPS, k=50, query_ids=np.arange(4) + 95000), kmax=50,
+                 ids=bids[:4], vals=bvals[:4], stream=sptr)  # warm-up
+        barrier()
+        bms = []
+        for bi in range(args.billion_batches):
+            Qb = probesim.make_queries(q25[bi * BB:(bi + 1) * BB], eps=EPS, k=50,
+                                       query_ids=[replica_query_id(rank, 900000 + bi * BB + j) for j in range(BB)])
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            G25.topk(Qb, kmax=50, ids=bids, vals=bvals, stream=sptr)
+            b.record(stream)
+            b.synchronize()
+            bms.append(a.elapsed_time(b))
+        barrier()
+        bst = G25.stats()
+        billion = {"graph": "R-MAT (.57,.19,.19,.05) n=2^25 m=%d (drawn on the GPU), seed 1" % m25,
+                   "queries": BB * args.billion_batches, "calls": args.billion_batches, "batch": BB, "eps": EPS,
+                   "k": 50, "probe": "switch (Sec. 4.4), c0=%g" % args.switch_c0,
+                   "value": BB * len(bms) / (sum(bms) / 1e3), "unit": "queries/s", "ms_per_call": bms,
+                   "n_r": int(G25.num_walks(EPS)), "generate_s": gen_s, "graph_create_s": create_s,
+                   "probes": bst["probes"], "switched": bst["switched"]}
+        G25.close()
+        del bids, bvals
+        torch.cuda.empty_cache()
+
     if rank != 0:
         if world > 1:
             torch.distributed.barrier()
@@ -595,6 +649,7 @@ def run_ours(args):
             "mixed_eps_topk": mixed,
             "serving": serving,
             "serving_2p23": serving23,
+            "billion_edge_topk": billion,
             "work": {"walks_per_query": agg["walks"] / args.steps, "tree_nodes_per_query": agg["tree_nodes"] / args.steps,
                      "vectors_per_query": agg["vectors"] / args.steps,
                      "edge_gathers_per_query": agg["edge_gathers"] / args.steps}}

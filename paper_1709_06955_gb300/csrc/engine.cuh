@@ -187,8 +187,6 @@ struct probesim_graph {
         std::lock_guard<std::mutex> lk(store_ptr_mu);
         store.swap(v);  // the old version is released outside the lock, by whichever reader holds it last
     }
-    // sorted keys (dst << 32 | src) of the initial edge set, freed once the store is built
-    std::vector<uint64_t> keys;
     std::vector<int32_t> h_ext2int;  // host copy of the id map (update batches are sorted by internal ids)
     // update scratch
     DevBuf u_batch, u_valid, u_vpre, u_delta, u_deg, u_part, u_hist;
@@ -197,8 +195,8 @@ struct probesim_graph {
     std::atomic<size_t> budget{0};  // device memory one call's working buffers may take (set while calls run)
     size_t budget0 = 0;  // the default: 60% of device memory at creation
     // pull launch shape chosen by probesim_autotune (defaults until then)
-    int32_t tune_wide = 32;       // widest tile (16 or 32 columns)
-    int32_t tune_bps[33] = {0};   // blocks per SM per tile width (0 = default 8)
+    int32_t tune_wide = 32;       // full tiles: 16, 32, or kPullPairs (32-column tiles two per pass)
+    int32_t tune_bps[65] = {0};   // blocks per SM per tile width, kPullPairs for the pairs (0 = default 8)
     int32_t tuned = 0;
 };
 

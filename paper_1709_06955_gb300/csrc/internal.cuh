@@ -189,7 +189,9 @@ void launch_zero_spare_row(float *MD, ColLayout L, int32_t width, cudaStream_t s
 // first tile's column in row 0; their rows are dpitch / pitch floats apart; tile j of D starts (j / dsub) * dts +
 // (j % dsub) * tile floats after the first, and likewise for MD with mts / msub (ColLayout::tile_stride/sub).
 // Row n of D (the spare row) must be zero over the pulled columns.
-// zmask (may be null): bit i of word k set = column 32k + i of the launch's columns is written as 0
+// zmask (may be null): bit i of word k set = column 32k + i of the launch's columns is written as 0.
+// tile = kPullPairs: 32-column tiles (ntiles of them, strides as for tile 32) taken two per pass.
+constexpr int32_t kPullPairs = 64;
 void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t dts, int32_t dsub, float *MD,
                  int32_t pitch, int64_t mts, int32_t msub, int32_t ntiles, int32_t tile, int32_t blocks_per_sm,
                  const uint32_t *zmask, cudaStream_t s);
@@ -327,6 +329,31 @@ void launch_upd_pieces(int32_t n, const long long *new_off, unsigned long long *
                        int32_t *split_v, unsigned long long *n_split, int32_t *pv, int64_t *pb, int32_t *pl,
                        cudaStream_t s);
 void launch_i64_copy(const long long *a, int64_t *b, int64_t count, cudaStream_t s);
+
+// device-side initial build of the graph store (graph_build.cu)
+int64_t radix_tiles(int64_t count);
+// Stable LSD radix sort of count keys by their low `bits` bits (8 per pass); tmp holds count keys, counts
+// 256 * radix_tiles(count) entries, offsets one more, partial scan64_partials_needed(that).  Returns the buffer
+// (keys or tmp) that holds the sorted keys.
+uint64_t *radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t count, int bits, long long *counts,
+                         long long *offsets, long long *partial, cudaStream_t s);
+void launch_build_keys(const int32_t *src, const int32_t *dst, int64_t m, int32_t n, int bs, uint64_t *keys,
+                       int32_t *bad, cudaStream_t s);
+void launch_build_flags(const uint64_t *keys, int64_t m, uint64_t end_key, long long *flag, cudaStream_t s);
+void launch_build_compact(const uint64_t *keys, int64_t m, uint64_t end_key, const long long *pre, uint64_t *out,
+                          cudaStream_t s);
+void launch_build_ext_off(const uint64_t *ukeys, int64_t mu, int32_t n, int bs, long long *ext_off, cudaStream_t s);
+void launch_build_outdeg(const uint64_t *ukeys, int64_t mu, uint32_t smask, unsigned long long *outdeg,
+                         cudaStream_t s);
+void launch_build_rank_keys(const unsigned long long *outdeg, int32_t n, int64_t mu, int bs, uint64_t *rk,
+                            cudaStream_t s);
+void launch_build_perm(const uint64_t *rk, int32_t n, uint32_t smask, const long long *ext_off,
+                       const unsigned long long *outdeg, int32_t *int2ext, int32_t *ext2int, long long *indeg_i,
+                       long long *outdeg_i, cudaStream_t s);
+void launch_build_in_col(int32_t n, const int32_t *int2ext, const long long *ext_off, const int64_t *in_off,
+                         const uint64_t *ukeys, uint32_t smask, const int32_t *ext2int, int bs, int32_t *in_col,
+                         uint64_t *okeys, cudaStream_t s);
+void launch_build_out_col(const uint64_t *okeys, int64_t mu, uint32_t smask, int32_t *out_col, cudaStream_t s);
 
 // sets the message probesim_last_error() returns on the calling thread
 void set_last_error(const char *msg);

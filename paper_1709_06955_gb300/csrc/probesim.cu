@@ -95,127 +95,126 @@ static bool is_device_ptr(const void *p) {
 // graph store
 // ------------------------------------------------------------------------------------------------
 
-// Builds the device graph store from the sorted unique keys (dst << 32 | src, external ids) and uploads it.
-// Internally nodes are renumbered by descending out-degree (ties by external id): the pull kernel gathers
-// score rows of in-neighbours, which are mostly high-out-degree nodes, so their rows become contiguous and
-// stay cached.  I(v) keeps its external source-id order (walks pick the k-th entry of that order) but holds
-// internal ids; O(x) holds internal ids in ascending order; ext2int / int2ext map at the boundary.
-static probesim_status upload_graph(probesim_graph *g, int32_t n, cudaStream_t st) {
-    const std::vector<uint64_t> &K = g->keys;
-    const int64_t m = (int64_t)K.size();
-    std::vector<int64_t> outdeg_ext(n, 0), ext_in_off(n + 1, 0);
-    for (int64_t e = 0; e < m; ++e) {
-        ext_in_off[(K[e] >> 32) + 1]++;
-        outdeg_ext[K[e] & 0xffffffffu]++;
-    }
-    for (int32_t v = 0; v < n; ++v) ext_in_off[v + 1] += ext_in_off[v];
-    std::vector<int32_t> int2ext(n), ext2int(n);
-    for (int32_t v = 0; v < n; ++v) int2ext[v] = v;
-    std::stable_sort(int2ext.begin(), int2ext.end(),
-                     [&](int32_t a, int32_t b) { return outdeg_ext[a] > outdeg_ext[b]; });
-    for (int32_t i = 0; i < n; ++i) ext2int[int2ext[i]] = i;
-    g->h_ext2int = ext2int;
-    std::vector<int64_t> in_off(n + 1, 0), out_off(n + 1, 0);
-    std::vector<int32_t> in_col(std::max<int64_t>(1, m)), out_col(std::max<int64_t>(1, m));
-    for (int32_t i = 0; i < n; ++i) {
-        const int32_t v = int2ext[i];
-        in_off[i + 1] = in_off[i] + (ext_in_off[v + 1] - ext_in_off[v]);
-        out_off[i + 1] = out_off[i] + outdeg_ext[v];
-    }
-    for (int32_t i = 0; i < n; ++i) {  // in-list of internal row i, in external source order
-        const int32_t v = int2ext[i];
-        int64_t pos = in_off[i];
-        for (int64_t e = ext_in_off[v]; e < ext_in_off[v + 1]; ++e) in_col[pos++] = ext2int[K[e] & 0xffffffffu];
-    }
-    {
-        std::vector<int64_t> cur(out_off.begin(), out_off.end() - 1);
-        for (int32_t i = 0; i < n; ++i)  // rows visited in internal order: out-rows fill in ascending internal id
-            for (int64_t e = in_off[i]; e < in_off[i + 1]; ++e) out_col[cur[in_col[e]]++] = i;
-    }
-    const float sc = (float)std::sqrt(g->cfg.c);
-    std::vector<float> w(n);
-    for (int32_t v = 0; v < n; ++v) {
-        const int64_t d = in_off[v + 1] - in_off[v];
-        w[v] = d > 0 ? sc / (float)d : 0.f;
-    }
-    // pieces: in-lists cut into at most kPiece edges; ordered by length, longest first (counting sort)
-    std::vector<int32_t> split;
-    std::vector<int64_t> per_len(kPiece + 2, 0);
-    for (int32_t v = 0; v < n; ++v) {
-        const int64_t d = in_off[v + 1] - in_off[v];
-        if (d > kPiece) {
-            split.push_back(v);
-            per_len[kPiece] += d / kPiece;
-            if (d % kPiece) per_len[d % kPiece] += 1;
-        } else {
-            per_len[d] += 1;
+// Builds the device graph store from the caller's edge list (device arrays of the caller's ids) with the kernels
+// of graph_build.cu and publishes it as the first version.  Repeated edges and loops are dropped.  Internally nodes
+// are renumbered by descending out-degree (ties by the caller's id): the pull kernel gathers score rows of
+// in-neighbours, which are mostly high-out-degree nodes, so their rows become contiguous and stay cached.  I(v)
+// keeps the caller's source-id order (walks pick the k-th entry of that order) but holds internal ids; O(x) holds
+// internal ids in ascending order; ext2int / int2ext map at the boundary.
+static probesim_status build_graph(probesim_graph *g, int32_t n, const int32_t *d_src, const int32_t *d_dst, int64_t m,
+                                   cudaStream_t st) {
+    struct Scratch {  // the build's temporaries, freed on every return
+        DevBuf ka, kb, kc, cnt, off, part, ext_off, outdeg, rka, rkb, indeg_i, outdeg_i, hist, flag;
+        ~Scratch() {
+            for (DevBuf *b : {&ka, &kb, &kc, &cnt, &off, &part, &ext_off, &outdeg, &rka, &rkb, &indeg_i, &outdeg_i,
+                              &hist, &flag})
+                b->release();
         }
-    }
-    std::vector<int64_t> start(kPiece + 2, 0);  // longest first: bucket kPiece, kPiece-1, ..., 0
-    for (int len = kPiece, acc = 0; len >= 0; --len) { start[len] = acc; acc += (int)per_len[len]; }
-    int64_t npieces = 0;
-    for (int len = 0; len <= kPiece; ++len) npieces += per_len[len];
-    std::vector<int32_t> pv(std::max<int64_t>(1, npieces)), pl(std::max<int64_t>(1, npieces));
-    std::vector<int64_t> pb(std::max<int64_t>(1, npieces));
-    {
-        std::vector<int64_t> cur(start);
-        auto put = [&](int32_t v, int64_t beg, int64_t len, bool sp) {
-            const int64_t i = cur[len]++;
-            pv[i] = v;
-            pb[i] = beg;
-            pl[i] = (int32_t)len | (sp ? (int32_t)0x80000000 : 0);
-        };
-        for (int32_t v = 0; v < n; ++v) {
-            const int64_t beg = in_off[v], d = in_off[v + 1] - beg;
-            if (d <= kPiece) { put(v, beg, d, false); continue; }
-            const int64_t full = d / kPiece, rest = d % kPiece;
-            for (int64_t c = 0; c < full; ++c) put(v, beg + c * kPiece, kPiece, true);
-            if (rest) put(v, beg + full * kPiece, rest, true);
-        }
-    }
-    pv.resize(npieces);
-    pb.resize(npieces);
-    pl.resize(npieces);
-    auto sv = std::make_shared<StoreVersion>();
-    PS_CUDA(sv->in_off.ensure(sizeof(int64_t) * (n + 1)));
-    PS_CUDA(sv->out_off.ensure(sizeof(int64_t) * (n + 1)));
-    PS_CUDA(sv->in_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m)));
-    PS_CUDA(sv->out_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, m)));
-    PS_CUDA(sv->w.ensure(sizeof(float) * n));
+    } t;
+    auto bitlen = [](uint64_t x) { int b = 0; while (x) { ++b; x >>= 1; } return b; };
+    const int bs = std::max(1, bitlen((uint64_t)std::max(1, n - 1)));  // bits of a node id
+    const uint32_t smask = (uint32_t)(((uint64_t)1 << bs) - 1);
+    const uint64_t end_key = (uint64_t)(uint32_t)n << bs;
+    const int64_t M = std::max<int64_t>(1, m);
+    const int64_t big = std::max<int64_t>(M, n);
+    const int64_t ntiles = radix_tiles(big);
+    PS_CUDA(t.ka.ensure(8 * (size_t)(M + 1)));
+    PS_CUDA(t.kb.ensure(8 * (size_t)(M + 1)));
+    PS_CUDA(t.cnt.ensure(8 * (size_t)(256 * ntiles)));
+    PS_CUDA(t.off.ensure(8 * (size_t)(256 * ntiles + 1)));
+    PS_CUDA(t.part.ensure(8 * (size_t)scan64_partials_needed(std::max<int64_t>(256 * ntiles, big + 1))));
+    PS_CUDA(t.flag.ensure(sizeof(int32_t)));
+    long long *cnt = t.cnt.as<long long>(), *off = t.off.as<long long>(), *part = t.part.as<long long>();
+    // 1-3: sorted unique edge keys (dst << bs | src, caller's ids)
+    PS_CUDA(cudaMemsetAsync(t.flag.p, 0, sizeof(int32_t), st));
+    launch_build_keys(d_src, d_dst, m, n, bs, t.ka.as<uint64_t>(), t.flag.as<int32_t>(), st);
+    int32_t bad = 0;
+    PS_CUDA(cudaMemcpyAsync(&bad, t.flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    if (bad) return fail(PROBESIM_E_RANGE, "edge id outside [0, n)");
+    uint64_t *sorted = radix_sort_u64(t.ka.as<uint64_t>(), t.kb.as<uint64_t>(), m, bs + bitlen(n), cnt, off, part, st);
+    long long *pre = reinterpret_cast<long long *>(sorted == t.ka.as<uint64_t>() ? t.kb.p : t.ka.p);
+    launch_build_flags(sorted, m, end_key, pre, st);
+    launch_scan64(pre, m, part, pre, st);  // in place: pre[m] = the number of distinct edges
+    long long mu_ll = 0;
+    PS_CUDA(cudaMemcpyAsync(&mu_ll, pre + std::max<int64_t>(0, m), sizeof(long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    const int64_t mu = m > 0 ? (int64_t)mu_ll : 0;
+    PS_CUDA(t.kc.ensure(8 * (size_t)std::max<int64_t>(1, mu)));
+    uint64_t *ukeys = t.kc.as<uint64_t>();
+    launch_build_compact(sorted, m, end_key, pre, ukeys, st);
+    // 4: in-list offsets and out-degrees by caller id, then the renumbering
+    PS_CUDA(t.ext_off.ensure(8 * ((size_t)n + 1)));
+    PS_CUDA(t.outdeg.ensure(8 * (size_t)n));
+    PS_CUDA(t.rka.ensure(8 * (size_t)n));
+    PS_CUDA(t.rkb.ensure(8 * (size_t)n));
+    PS_CUDA(t.indeg_i.ensure(8 * (size_t)n));
+    PS_CUDA(t.outdeg_i.ensure(8 * (size_t)n));
+    long long *ext_off = t.ext_off.as<long long>();
+    unsigned long long *outdeg = t.outdeg.as<unsigned long long>();
+    PS_CUDA(cudaMemsetAsync(outdeg, 0, 8 * (size_t)n, st));
+    launch_build_ext_off(ukeys, mu, n, bs, ext_off, st);
+    launch_build_outdeg(ukeys, mu, smask, outdeg, st);
+    launch_build_rank_keys(outdeg, n, mu, bs, t.rka.as<uint64_t>(), st);
+    const uint64_t *rk =
+        radix_sort_u64(t.rka.as<uint64_t>(), t.rkb.as<uint64_t>(), n, bs + bitlen((uint64_t)mu), cnt, off, part, st);
     PS_CUDA(g->ext2int.ensure(sizeof(int32_t) * n));
     PS_CUDA(g->int2ext.ensure(sizeof(int32_t) * n));
-    PS_CUDA(sv->piece_v.ensure(sizeof(int32_t) * std::max<size_t>(1, pv.size())));
-    PS_CUDA(sv->piece_beg.ensure(sizeof(int64_t) * std::max<size_t>(1, pb.size())));
-    PS_CUDA(sv->piece_len.ensure(sizeof(int32_t) * std::max<size_t>(1, pl.size())));
-    PS_CUDA(sv->split_v.ensure(sizeof(int32_t) * std::max<size_t>(1, split.size())));
-    PS_CUDA(cudaMemcpyAsync(sv->in_off.p, in_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(sv->out_off.p, out_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
-    if (m > 0) {
-        PS_CUDA(cudaMemcpyAsync(sv->in_col.p, in_col.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
-        PS_CUDA(cudaMemcpyAsync(sv->out_col.p, out_col.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
-    }
-    PS_CUDA(cudaMemcpyAsync(sv->w.p, w.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(g->ext2int.p, ext2int.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(g->int2ext.p, int2ext.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(sv->piece_v.p, pv.data(), sizeof(int32_t) * pv.size(), cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(sv->piece_beg.p, pb.data(), sizeof(int64_t) * pb.size(), cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(sv->piece_len.p, pl.data(), sizeof(int32_t) * pl.size(), cudaMemcpyHostToDevice, st));
-    if (!split.empty())
-        PS_CUDA(cudaMemcpyAsync(sv->split_v.p, split.data(), sizeof(int32_t) * split.size(), cudaMemcpyHostToDevice, st));
+    launch_build_perm(rk, n, smask, ext_off, outdeg, g->int2ext.as<int32_t>(), g->ext2int.as<int32_t>(),
+                      t.indeg_i.as<long long>(), t.outdeg_i.as<long long>(), st);
+    // 5: the CSR arrays in internal ids
+    auto sv = std::make_shared<StoreVersion>();
+    PS_CUDA(sv->in_off.ensure(sizeof(int64_t) * ((size_t)n + 1)));
+    PS_CUDA(sv->out_off.ensure(sizeof(int64_t) * ((size_t)n + 1)));
+    PS_CUDA(sv->in_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, mu)));
+    PS_CUDA(sv->out_col.ensure(sizeof(int32_t) * std::max<int64_t>(1, mu)));
+    launch_scan64(t.indeg_i.as<long long>(), n, part, sv->in_off.as<long long>(), st);
+    launch_scan64(t.outdeg_i.as<long long>(), n, part, sv->out_off.as<long long>(), st);
+    uint64_t *okeys = t.ka.as<uint64_t>();  // the edge-key buffers are free again (the unique keys live in kc)
+    launch_build_in_col(n, g->int2ext.as<int32_t>(), ext_off, sv->in_off.as<int64_t>(), ukeys, smask,
+                        g->ext2int.as<int32_t>(), bs, sv->in_col.as<int32_t>(), okeys, st);
+    const uint64_t *osorted = radix_sort_u64(okeys, t.kb.as<uint64_t>(), mu, 2 * bs, cnt, off, part, st);
+    launch_build_out_col(osorted, mu, smask, sv->out_col.as<int32_t>(), st);
+    // w and the pull pieces (in-lists cut into at most kPiece edges, longest first)
+    const int64_t cap_pieces = (int64_t)n + mu / kPiece + 1;
+    PS_CUDA(sv->w.ensure(sizeof(float) * n));
+    PS_CUDA(sv->piece_v.ensure(sizeof(int32_t) * cap_pieces));
+    PS_CUDA(sv->piece_beg.ensure(sizeof(int64_t) * cap_pieces));
+    PS_CUDA(sv->piece_len.ensure(sizeof(int32_t) * cap_pieces));
+    PS_CUDA(sv->split_v.ensure(sizeof(int32_t) * (size_t)n));
+    PS_CUDA(t.hist.ensure(sizeof(unsigned long long) * (2 * (kPiece + 1) + 2)));
+    launch_upd_w(n, sv->in_off.as<long long>(), (float)std::sqrt(g->cfg.c), sv->w.as<float>(),
+                 t.indeg_i.as<long long>(), st);
+    unsigned long long *hist = t.hist.as<unsigned long long>(), *cursor = hist + (kPiece + 1),
+                       *nsplit = cursor + (kPiece + 1);
+    launch_upd_pieces(n, sv->in_off.as<long long>(), hist, cursor, sv->split_v.as<int32_t>(), nsplit,
+                      sv->piece_v.as<int32_t>(), sv->piece_beg.as<int64_t>(), sv->piece_len.as<int32_t>(), st);
+    std::vector<unsigned long long> hh(kPiece + 2);
+    long long ends[2] = {0, 0};
+    PS_CUDA(cudaMemcpyAsync(hh.data(), hist, sizeof(unsigned long long) * (kPiece + 1), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(hh.data() + kPiece + 1, nsplit, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(&ends[0], sv->in_off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(&ends[1], sv->out_off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st));
+    g->h_ext2int.resize(n);
+    PS_CUDA(cudaMemcpyAsync(g->h_ext2int.data(), g->ext2int.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaGetLastError());
     PS_CUDA(cudaStreamSynchronize(st));
+    if (ends[0] != mu || ends[1] != mu) return fail(PROBESIM_E_CUDA, "internal: the built lists disagree on m");
+    int64_t npieces = 0;
+    for (int len = 0; len <= kPiece; ++len) npieces += (int64_t)hh[len];
     DeviceGraph &d = sv->dg;
     d.n = n;
-    d.m = m;
+    d.m = mu;
     d.in_off = sv->in_off.as<int64_t>();
     d.in_col = sv->in_col.as<int32_t>();
     d.out_off = sv->out_off.as<int64_t>();
     d.out_col = sv->out_col.as<int32_t>();
     d.w = sv->w.as<float>();
-    d.n_pieces = (int64_t)pv.size();
+    d.n_pieces = npieces;
     d.piece_v = sv->piece_v.as<int32_t>();
     d.piece_beg = sv->piece_beg.as<int64_t>();
     d.piece_len = sv->piece_len.as<int32_t>();
-    d.n_split = (int32_t)split.size();
+    d.n_split = (int32_t)hh[kPiece + 1];
     d.split_v = sv->split_v.as<int32_t>();
     d.ext2int = g->ext2int.as<int32_t>();
     d.int2ext = g->int2ext.as<int32_t>();
@@ -689,7 +688,9 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     PS_CUDA(ws->md_b.ensure((size_t)max_floats * sizeof(float)));
     float *A = ws->md_a.as<float>(), *Bm = ws->md_b.as<float>();
     const int32_t *node_list = ws->node_list.as<int32_t>();
-    const int32_t wide = g->tune_wide == 16 ? 16 : 32;
+    // the full tiles' launch: 32-column tiles, their 16-column halves, or 32-column tiles two per pass
+    const int32_t wide = g->tune_wide == 16 || g->tune_wide == kPullPairs ? g->tune_wide : 32;
+    const int32_t tw = wide == kPullPairs ? 32 : wide;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks;
     // Without profiling, the push block and the tail tile of a depth run on a second stream beside the
     // accumulate and the full-tile pull: they write other columns of A than the full tiles do.  With
@@ -758,10 +759,10 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
                             tail[d], g->tune_bps[tail[d]], zmask_at(d) ? zmask_at(d) + nfull[d] : nullptr, ss);
                 ++launches;
             }
-            if (nfull[d] > 0) {  // 32-column tiles (or their 16-column halves)
-                const int32_t nt = nfull[d] * (32 / wide);
-                launch_pull(dg, Bm, Lb.rpitch(0), Lb.tile_stride(), Lb.tile_sub(wide), A, La.rpitch(0), La.tile_stride(),
-                            La.tile_sub(wide), nt, wide, g->tune_bps[wide], zmask_at(d), st);
+            if (nfull[d] > 0) {  // 32-column tiles (or their 16-column halves, or pairs of them)
+                const int32_t nt = nfull[d] * (32 / tw);
+                launch_pull(dg, Bm, Lb.rpitch(0), Lb.tile_stride(), Lb.tile_sub(tw), A, La.rpitch(0), La.tile_stride(),
+                            La.tile_sub(tw), nt, wide, g->tune_bps[wide], zmask_at(d), st);
                 ++launches;
             }
             if (ws->profiling) {
@@ -1412,11 +1413,6 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
     if (!(c.eps_p >= 0.f) || !(c.c0 >= 0.f) || !(c.shift >= 0.f))
         return fail(PROBESIM_E_INVALID, "eps_p, c0 and shift must be >= 0");
     if (c.probe_mode < 0 || c.probe_mode > 2) return fail(PROBESIM_E_INVALID, "unknown probe_mode");
-    std::vector<int32_t> hs, hd;
-    PS_TRY(fetch_ids(src, m, hs));
-    PS_TRY(fetch_ids(dst, m, hd));
-    for (int64_t e = 0; e < m; ++e)
-        if (hs[e] < 0 || hs[e] >= n || hd[e] < 0 || hd[e] >= n) return fail(PROBESIM_E_RANGE, "edge id outside [0, n)");
     probesim_graph *g = new (std::nothrow) probesim_graph();
     if (!g) return fail(PROBESIM_E_NOMEM, "host allocation failed");
     g->cfg = c;
@@ -1431,17 +1427,33 @@ probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32
         delete g;
         return fail(PROBESIM_E_NOMEM, "pinned host allocation failed");
     }
-    g->keys.reserve(m);
-    for (int64_t e = 0; e < m; ++e)
-        if (hs[e] != hd[e]) g->keys.push_back(((uint64_t)(uint32_t)hd[e] << 32) | (uint32_t)hs[e]);
-    std::sort(g->keys.begin(), g->keys.end());
-    g->keys.erase(std::unique(g->keys.begin(), g->keys.end()), g->keys.end());
-    probesim_status s = upload_graph(g, n, (cudaStream_t)stream);
+    probesim_status s;
+    {   // the edge list on the device (copied there when the caller's arrays are on the host), then the build
+        const bool on_dev = m == 0 || (is_device_ptr(src) && is_device_ptr(dst));
+        DevBuf staged;
+        const int32_t *d_src = src, *d_dst = dst;
+        s = PROBESIM_OK;
+        if (!on_dev) {
+            cudaError_t e = staged.ensure(2 * sizeof(int32_t) * (size_t)m);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(staged.p, src, sizeof(int32_t) * m, cudaMemcpyDefault, (cudaStream_t)stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(staged.as<int32_t>() + m, dst, sizeof(int32_t) * m, cudaMemcpyDefault,
+                                    (cudaStream_t)stream);
+            if (e != cudaSuccess)
+                s = fail(e == cudaErrorMemoryAllocation ? PROBESIM_E_NOMEM : PROBESIM_E_CUDA,
+                         std::string("staging the edge list: ") + cudaGetErrorString(e));
+            d_src = staged.as<int32_t>();
+            d_dst = staged.as<int32_t>() + m;
+        }
+        if (s == PROBESIM_OK) s = build_graph(g, n, d_src, d_dst, m, (cudaStream_t)stream);
+        cudaStreamSynchronize((cudaStream_t)stream);
+        staged.release();
+    }
     if (s != PROBESIM_OK) {
         probesim_graph_destroy(g);
         return s;
     }
-    std::vector<uint64_t>().swap(g->keys);  // later updates merge on the device
     {   // update batches allocate store versions from the device's stream-ordered pool: let it keep about three
         // versions' worth of memory between updates instead of returning it to the driver at every synchronisation
         cudaMemPool_t pool;
@@ -1831,8 +1843,8 @@ probesim_status probesim_topk(probesim_graph *g, const probesim_query *q, int32_
 }
 
 // Times the pull on this graph's in-lists for every tile width in {1, 2, 4, 8, 16, 32} and blocks-per-SM in
-// {2, 4, 8, 16} over a random score matrix, keeps the fastest shape per width, and picks the widest tile (16
-// or 32) by time per column.  The choice is stored in the graph and used by every later query.
+// {2, 4, 8, 16} over a random score matrix, keeps the fastest shape per width, and picks the full tiles' launch
+// (16-column halves, 32-column tiles, or 32-column tiles two per pass) by time per column.  The choice is stored in the graph and used by every later query.
 probesim_status probesim_autotune(probesim_graph *g, void *stream) {
     if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
     std::lock_guard<std::mutex> lk(g->mu);
@@ -1871,13 +1883,14 @@ probesim_status probesim_autotune(probesim_graph *g, void *stream) {
             if (ms < best) best = ms, g->tune_bps[T] = bps;
         }
     }
-    // wide tiles: two 32-column tiles of a node-major [n][64] matrix, as 32-column tiles or 16-column halves
-    double per_col[33] = {0};
-    int32_t wide_bps[33] = {0};
-    for (int32_t T : {16, 32}) {
+    // wide tiles: two 32-column tiles of a node-major [n][64] matrix, as 32-column tiles, 16-column halves, or one
+    // pass over both
+    double per_col[kPullPairs + 1] = {0};
+    int32_t wide_bps[kPullPairs + 1] = {0};
+    for (int32_t T : {16, 32, kPullPairs}) {
         float best = 1e30f;
         for (int32_t bps : bpss) {
-            const int32_t nt = 2 * (32 / T);
+            const int32_t nt = T == 16 ? 4 : 2;
             const float ms =
                 time_pull([&] { launch_pull(dg, Da, P, 0, 1 << 30, Mb, P, 0, 1 << 30, nt, T, bps, nullptr, st); });
             if (ms < best) best = ms, wide_bps[T] = bps;
@@ -1885,11 +1898,31 @@ probesim_status probesim_autotune(probesim_graph *g, void *stream) {
         per_col[T] = best / 3.0 / 64.0;
     }
     PS_CUDA(cudaGetLastError());
+    int32_t pick = 32;
+    for (int32_t T : {16, kPullPairs})
+        if (per_col[T] < per_col[pick]) pick = T;
     g->tune_bps[32] = wide_bps[32];
-    if (per_col[16] < per_col[32]) g->tune_bps[16] = wide_bps[16];
-    g->tune_wide = per_col[16] < per_col[32] ? 16 : 32;
+    g->tune_bps[pick] = wide_bps[pick];
+    g->tune_wide = pick;
     g->tuned = 1;
     PS_CUDA(cudaGetLastError());
+    return PROBESIM_OK;
+}
+
+probesim_status probesim_set_tuning(probesim_graph *g, int32_t wide_tile, const int32_t *blocks_per_sm) {
+    if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
+    if (wide_tile != 16 && wide_tile != 32 && wide_tile != kPullPairs)
+        return fail(PROBESIM_E_INVALID, "wide_tile must be 16, 32 or 64");
+    if (blocks_per_sm)
+        for (int i = 0; i < 7; ++i)
+            if (blocks_per_sm[i] < 1 || blocks_per_sm[i] > 32)
+                return fail(PROBESIM_E_INVALID, "blocks_per_sm must lie in [1, 32]");
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->tune_wide = wide_tile;
+    if (blocks_per_sm) {
+        for (int i = 0; i < 6; ++i) g->tune_bps[1 << i] = blocks_per_sm[i];
+        g->tune_bps[kPullPairs] = blocks_per_sm[6];
+    }
     return PROBESIM_OK;
 }
 

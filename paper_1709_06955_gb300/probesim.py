@@ -22,6 +22,7 @@ EXPORTS = [
     "probesim_last_error", "probesim_topk_select_noalloc", "probesim_server_config_default",
     "probesim_server_create", "probesim_server_submit", "probesim_server_update", "probesim_server_poll",
     "probesim_server_get_stats", "probesim_server_destroy", "probesim_autotune", "probesim_get_tuning",
+    "probesim_set_tuning",
     "probesim_set_memory_budget", "probesim_split_error", "probesim_pair_mc",
 ]
 
@@ -127,6 +128,7 @@ def load(path=None):
     L.probesim_server_destroy.argtypes = [vp]
     L.probesim_autotune.argtypes = [vp, vp]
     L.probesim_get_tuning.argtypes = [vp, P(C.c_int32), P(C.c_int32)]
+    L.probesim_set_tuning.argtypes = [vp, C.c_int32, P(C.c_int32)]
     for name in EXPORTS:
         if name != "probesim_last_error":
             getattr(L, name).restype = C.c_int
@@ -336,6 +338,17 @@ class Graph:
         bps = (C.c_int32 * 6)()
         _check(load().probesim_get_tuning(self._h, C.byref(wide), bps))
         return {"wide_tile": wide.value, "blocks_per_sm": {1 << i: bps[i] for i in range(6)}}
+
+    def set_tuning(self, wide_tile, blocks_per_sm=None):
+        """Sets the pull's launch shape by hand (probesim_set_tuning): wide_tile 16, 32 or 64 (32-column tiles two
+        per pass); blocks_per_sm, if given, 7 values for tile widths 1..32 and the pairs."""
+        arr = None
+        if blocks_per_sm is not None:
+            vals = [int(b) for b in blocks_per_sm]
+            if len(vals) != 7:
+                raise ValueError("blocks_per_sm needs 7 values")
+            arr = (C.c_int32 * 7)(*vals)
+        _check(load().probesim_set_tuning(self._h, int(wide_tile), arr))
 
     def set_memory_budget(self, nbytes):
         """Device memory one call's working buffers may take (0 = the default, 60% of the device)."""

@@ -105,9 +105,11 @@ def queries(n, dst, count, seed=2):
     """``count`` query nodes drawn uniformly (without replacement when possible) from the nodes
     with at least one in-neighbour."""
     rng = np.random.default_rng(seed)
-    if type(dst).__module__.startswith("torch"):
-        dst = dst.cpu().numpy()
-    indeg = np.bincount(np.asarray(dst, dtype=np.int64), minlength=n)
+    if type(dst).__module__.startswith("torch"):  # counted where the edges live (10^9 of them at the largest size)
+        import torch
+        indeg = torch.bincount(dst.to(torch.int64), minlength=n).cpu().numpy()
+    else:
+        indeg = np.bincount(np.asarray(dst, dtype=np.int64), minlength=n)
     cand = np.nonzero(indeg > 0)[0]
     if cand.size == 0:
         raise ValueError("graph has no node with an in-neighbour")
