@@ -76,9 +76,8 @@ def parse():
                     help="calls of 64 top-50 queries on R-MAT 2^25 with 10^9 edges (0 = off)")
     ap.add_argument("--billion-edges", type=float, default=1e9, help="edges of that graph")
     ap.add_argument("--accuracy-queries", type=int, default=5, help="queries of the pooling accuracy leg (0 = off)")
-    ap.add_argument("--profile-case", choices=["frontier"], default=None,
-                    help="run one small case for an ncu capture and exit (frontier: R-MAT 2^20 drawn on the GPU, "
-                         "switch mode c0 = 0.01, two calls of four queries at eps = 0.1)")
+    ap.add_argument("--profile-case", choices=["frontier", "billion"], default=None,
+                    help="run one fixed case for an ncu capture and exit (see profile_case)")
     return ap.parse_args()
 
 
@@ -470,17 +469,19 @@ def run_ours(args):
         from paper_1709_06955_gb300 import accuracy as A
         t0 = time.perf_counter()
         per = {m: [] for m in acc_lists}
-        pool_sizes = []
+        pool_sizes, ranks = [], []
         for t, u in enumerate(acc_nodes):
             truth, score = A.pool(G, int(u), [acc_lists[m][t] for m in acc_lists], 50, eps=2e-4, delta=1e-4,
                                   key_base=(1 << 30) + 4096 * t)
             pool_sizes.append(len(score))
+            ranks.append([score[int(truth[i])] for i in (0, 9, min(49, len(truth) - 1))])
             for m in acc_lists:
                 per[m].append(A.evaluate(acc_lists[m][t], truth, lambda v, sc=score: sc.get(v, 0.0)))
         accuracy = {"queries": len(acc_nodes), "k": 50, "eps": EPS,
                     "expert": "pairwise Monte Carlo on the GPU, eps 2e-4, delta 1e-4 (%d walk pairs per node)"
                               % A.mc_walk_pairs(2e-4, 1e-4),
                     "mean_pool": float(np.mean(pool_sizes)), "seconds": time.perf_counter() - t0,
+                    "truth_scores_at_rank_1_10_50": [float(x) for x in np.mean(np.array(ranks), axis=0)],
                     "methods": {m: {k: float(np.mean([r[k] for r in per[m]])) for k in ("precision", "ndcg", "tau")}
                                 for m in per}}
 
@@ -662,21 +663,38 @@ def run_ours(args):
 
 
 def profile_case(args):
-    """A small, fixed invocation of one engine for kernel captures (no timing, no JSON line)."""
+    """A small, fixed invocation of one engine for kernel captures (no timing, no JSON line).
+
+    frontier: R-MAT 2^20 drawn on the GPU, switch mode c0 = 0.01, two calls of four queries at eps = 0.1.
+    billion:  R-MAT 2^25 with 10^9 edges drawn and built on the GPU, switch mode c0 = 0.01, one call of 64 top-50
+              queries at eps = 0.1 (the billion-edge leg's call)."""
     import numpy as np
     import torch
     from paper_1709_06955_gb300 import build, probesim, synth
     build.build()
-    n, s, d = synth.rmat_device(20, 16 << 20, seed=1)
-    torch.cuda.empty_cache()
-    qs = synth.queries(n, d, 8, seed=2)
-    G = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_SWITCH, c0=0.01)
-    out = torch.zeros((4, n), dtype=torch.float32, device="cuda")
-    for i in range(2):
-        G.single_source(probesim.make_queries(qs[4 * i:4 * i + 4], eps=EPS, query_ids=np.arange(4) + 4 * i), out=out)
+    if args.profile_case == "billion":
+        n, s, d = synth.rmat_device(25, int(args.billion_edges), seed=1)
+        torch.cuda.empty_cache()
+        qs = synth.queries(n, d, 64, seed=2)
+        G = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_SWITCH, c0=0.01)
+        del s, d
+        torch.cuda.empty_cache()
+        ids = torch.empty((64, 50), dtype=torch.int32, device="cuda")
+        vals = torch.empty((64, 50), dtype=torch.float32, device="cuda")
+        G.topk(probesim.make_queries(qs, eps=EPS, k=50, query_ids=np.arange(64) + 900000), kmax=50, ids=ids, vals=vals)
+    else:
+        n, s, d = synth.rmat_device(20, 16 << 20, seed=1)
+        torch.cuda.empty_cache()
+        qs = synth.queries(n, d, 8, seed=2)
+        G = probesim.Graph(n, s, d, probe_mode=probesim.PROBE_SWITCH, c0=0.01)
+        out = torch.zeros((4, n), dtype=torch.float32, device="cuda")
+        for i in range(2):
+            G.single_source(probesim.make_queries(qs[4 * i:4 * i + 4], eps=EPS, query_ids=np.arange(4) + 4 * i),
+                            out=out)
     torch.cuda.synchronize()
-    print("profile case %s done: %d deterministic edge pushes, %d levels" % (args.profile_case, G.stats()["edge_gathers"],
-                                                                          G.stats()["levels"]))
+    st = G.stats()
+    print("profile case %s done: %d deterministic edge pushes, %d levels, %d of %d probes switched"
+          % (args.profile_case, st["edge_gathers"], st["levels"], st["switched"], st["probes"]))
     return 0
 
 
