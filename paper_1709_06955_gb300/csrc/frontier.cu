@@ -10,7 +10,8 @@
 //   expand   every kept entry x pushes sqrt(c)/|I(v)| * Score(x) to each v in O(x), v != u_{q-j-1}, into
 //            the probe's region of the next level's table -- open addressing over a power of two, or a
 //            dense slab of n slots when the probe's out-degree sum is a sizeable fraction of n -- or, at
-//            the probe's last level (j = q-2), straight into its query's estimate with weight w
+//            the probe's last level (j = q-2), straight into its query's estimate with weight w; a slot holds
+//            its node and its sum in one 16-byte pair, so the sum's atomic finds the sector the key lookup loaded
 //   compact  the regions' occupied slots, in slot order, become H_{j+1}, still grouped by probe; the compaction
 //            empties the slots it reads, so the table needs no clearing between passes
 // Work items are (entry, out-edge) pairs balanced by prefix sums over the entries' out-degrees, so a hub's
@@ -187,19 +188,22 @@ __global__ void __launch_bounds__(kThreads) k_fr_expand(DeviceGraph g, TrieTable
                 continue;
             }
             const long long off = P.roff[p] - a.rbase, R = P.roff[p + 1] - P.roff[p];
+            const int32_t key = v + 1;
             if (P.state[p] & kProbeDense) {
-                a.keys[off + v] = v;
-                atomicAdd(a.vals + off + v, (unsigned long long)c);
+                FrontierSlot &slot = a.tab[off + v];
+                slot.key = key;
+                atomicAdd(&slot.val, (unsigned long long)c);
             } else {
                 long long h = node_hash(v) & (R - 1);
                 for (long long probe = 0; probe < R; ++probe) {
-                    int32_t cur = a.keys[off + h];
-                    if (cur == -1) {
-                        cur = atomicCAS(a.keys + off + h, -1, v);
-                        if (cur == -1) cur = v;
+                    FrontierSlot &slot = a.tab[off + h];
+                    int32_t cur = slot.key;
+                    if (cur == 0) {
+                        cur = atomicCAS(&slot.key, 0, key);
+                        if (cur == 0) cur = key;
                     }
-                    if (cur == v) {
-                        atomicAdd(a.vals + off + h, (unsigned long long)c);
+                    if (cur == key) {
+                        atomicAdd(&slot.val, (unsigned long long)c);
                         break;
                     }
                     h = (h + 1) & (R - 1);
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) k_fr_expand(DeviceGraph g, TrieTable
 }
 
 // occupied slots per block of kCompactTile table slots
-__global__ void __launch_bounds__(kThreads) k_fr_count(const int32_t *__restrict__ keys, long long T,
+__global__ void __launch_bounds__(kThreads) k_fr_count(const FrontierSlot *__restrict__ tab, long long T,
                                                        long long *__restrict__ bcount) {
     __shared__ int s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_fr_count(const int32_t *__restrict
     int c = 0;
     for (int i = threadIdx.x; i < kCompactTile; i += blockDim.x) {
         const long long k = base + i;
-        if (k < T && keys[k] >= 0) ++c;
+        if (k < T && tab[k].key != 0) ++c;
     }
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(&s_cnt, c);
@@ -230,8 +234,7 @@ __global__ void __launch_bounds__(kThreads) k_fr_count(const int32_t *__restrict
 
 // writes the occupied slots of each block, in slot order, at out_base + bpre[block], and empties them again, so
 // the table is clean for the next pass without a memset
-__global__ void __launch_bounds__(kThreads) k_fr_write(int32_t *__restrict__ keys, unsigned long long *__restrict__ vals,
-                                                       long long T,
+__global__ void __launch_bounds__(kThreads) k_fr_write(FrontierSlot *__restrict__ tab, long long T,
                                                        const long long *__restrict__ roff, int32_t p0, int32_t p1,
                                                        long long rbase, const long long *__restrict__ bpre,
                                                        FrontierList out, long long out_base, long long out_cap) {
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_fr_write(int32_t *__restrict__ key
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = 0; r < kCompactTile; r += kThreads) {
         const long long k = base + r + threadIdx.x;
-        const bool occ = k < T && keys[k] >= 0;
+        const bool occ = k < T && tab[k].key != 0;
         const unsigned m = __ballot_sync(0xffffffffu, occ);
         if (lane == 0) s_warp[warp] = __popc(m);
         __syncthreads();
@@ -279,13 +282,10 @@ __global__ void __launch_bounds__(kThreads) k_fr_write(int32_t *__restrict__ key
                 if (roff[mid] - rbase <= k) lo = mid; else hi = mid;
             }
             out.p[pos] = lo;
-            out.x[pos] = keys[k];
-            out.val[pos] = fx_to_f((long long)vals[k]);
+            out.x[pos] = tab[k].key - 1;
+            out.val[pos] = fx_to_f((long long)tab[k].val);
         }
-        if (occ) {
-            keys[k] = -1;
-            vals[k] = 0;
-        }
+        if (occ) *reinterpret_cast<ulonglong2 *>(tab + k) = make_ulonglong2(0ull, 0ull);
         __syncthreads();
         if (threadIdx.x == 0) s_run += total;
         __syncthreads();
@@ -369,14 +369,14 @@ void launch_fr_expand(const DeviceGraph &g, TrieTable t, FrontierProbes P, Front
     k_fr_expand<<<blocks, kThreads, 0, s>>>(g, t, P, F, a);
 }
 int64_t fr_compact_blocks(long long T) { return (T + kCompactTile - 1) / kCompactTile; }
-void launch_fr_count(const int32_t *keys, long long T, long long *bcount, cudaStream_t s) {
-    if (T > 0) k_fr_count<<<(unsigned)fr_compact_blocks(T), kThreads, 0, s>>>(keys, T, bcount);
+void launch_fr_count(const FrontierSlot *tab, long long T, long long *bcount, cudaStream_t s) {
+    if (T > 0) k_fr_count<<<(unsigned)fr_compact_blocks(T), kThreads, 0, s>>>(tab, T, bcount);
 }
-void launch_fr_write(int32_t *keys, unsigned long long *vals, long long T, const long long *roff, int32_t p0,
+void launch_fr_write(FrontierSlot *tab, long long T, const long long *roff, int32_t p0,
                      int32_t p1, long long rbase, const long long *bpre, FrontierList out, long long out_base,
                      long long out_cap, cudaStream_t s) {
     if (T > 0)
-        k_fr_write<<<(unsigned)fr_compact_blocks(T), kThreads, 0, s>>>(keys, vals, T, roff, p0, p1, rbase, bpre, out,
+        k_fr_write<<<(unsigned)fr_compact_blocks(T), kThreads, 0, s>>>(tab, T, roff, p0, p1, rbase, bpre, out,
                                                                        out_base, out_cap);
 }
 void launch_fr_advance(TrieTable t, FrontierProbes P, int32_t p0, int32_t p1, cudaStream_t s) {

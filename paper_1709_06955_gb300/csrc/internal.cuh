@@ -236,13 +236,19 @@ struct FrontierList {  // entries of the frontiers, grouped by probe in probe or
     int32_t *x = nullptr;
     float *val = nullptr;                 // score (the fixed-point sum of its level, rounded to FP32)
 };
+// One slot of a level's table: node + 1 (0 = empty) and the node's score sum (2^-44 units), in 16 bytes of one
+// sector, so the sum's atomic lands in the sector that the key's lookup has just brought into the L2.
+struct alignas(16) FrontierSlot {
+    int32_t key;
+    int32_t pad;
+    unsigned long long val;
+};
 struct FrontierExpand {
     const long long *wp = nullptr;        // [nF+1] prefix sums of the entries' work (out-degrees)
     int64_t f_lo = 0, f_hi = 0;           // entries of this pass
     long long e_lo = 0, e_hi = 0;         // work items of this pass
     int32_t j = 0;                        // level
-    int32_t *keys = nullptr;              // next level's table: node per slot, -1 empty (empty between passes)
-    unsigned long long *vals = nullptr;   // score per slot (2^-44 units)
+    FrontierSlot *tab = nullptr;          // next level's table (all slots empty between passes)
     long long rbase = 0;                  // table offset of this pass's first region
     unsigned long long *acc = nullptr;    // [B][n] estimates (2^-44 units, internal ids)
     int32_t n = 0;
@@ -258,8 +264,8 @@ void launch_fr_work(FrontierList F, int64_t nF, FrontierProbes P, long long *wor
 void launch_fr_expand(const DeviceGraph &g, TrieTable t, FrontierProbes P, FrontierList F, const FrontierExpand &a,
                       cudaStream_t s);
 int64_t fr_compact_blocks(long long T);
-void launch_fr_count(const int32_t *keys, long long T, long long *bcount, cudaStream_t s);
-void launch_fr_write(int32_t *keys, unsigned long long *vals, long long T, const long long *roff, int32_t p0,
+void launch_fr_count(const FrontierSlot *tab, long long T, long long *bcount, cudaStream_t s);
+void launch_fr_write(FrontierSlot *tab, long long T, const long long *roff, int32_t p0,
                      int32_t p1, long long rbase, const long long *bpre, FrontierList out, long long out_base,
                      long long out_cap, cudaStream_t s);
 void launch_fr_advance(TrieTable t, FrontierProbes P, int32_t p0, int32_t p1, cudaStream_t s);

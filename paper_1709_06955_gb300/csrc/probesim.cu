@@ -1114,7 +1114,8 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     // level whose next frontier might not fit the list budget processes the passes that fit and defers the other
     // probes, with their level-j entries, to a stack; they resume once the processed range has run out.  Every
     // probe's last-level pushes land in the estimate exactly once, whatever the split.
-    const long long pass_slots = std::max<long long>((long long)n, (long long)(budget_of(g, ws) / 4 / 12));
+    const long long pass_slots =
+        std::max<long long>((long long)n, (long long)(budget_of(g, ws) / 4 / sizeof(FrontierSlot)));
     const long long list_cap = std::max<long long>((long long)n, (long long)(budget_of(g, ws) / 8 / 12));
     auto list_of = [&](int k) {
         FrontierList F;
@@ -1215,12 +1216,10 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
         ws->stats.max_table_slots = std::max<int64_t>(ws->stats.max_table_slots, T);
         const long long tslots = std::max<long long>(1, std::min<long long>(T, pass_slots + n));
         {
-            const void *k0 = ws->f_keys.p, *v0 = ws->f_vals.p;
-            PS_ALLOC(ws->f_keys.ensure(sizeof(int32_t) * tslots));
-            PS_ALLOC(ws->f_vals.ensure(sizeof(unsigned long long) * tslots));
-            if (ws->f_keys.p != k0 || ws->f_vals.p != v0 || !ws->f_table_clean) {  // new memory, or a failed call
-                PS_CUDA(cudaMemsetAsync(ws->f_keys.p, 0xFF, ws->f_keys.cap, st));   // left slots behind: clear it
-                PS_CUDA(cudaMemsetAsync(ws->f_vals.p, 0, ws->f_vals.cap, st));
+            const void *k0 = ws->f_keys.p;
+            PS_ALLOC(ws->f_keys.ensure(sizeof(FrontierSlot) * tslots));
+            if (ws->f_keys.p != k0 || !ws->f_table_clean) {  // new memory, or a failed call left slots behind
+                PS_CUDA(cudaMemsetAsync(ws->f_keys.p, 0, ws->f_keys.cap, st));
                 ws->f_table_clean = true;
             }
         }
@@ -1255,8 +1254,7 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
             a.e_lo = e_lo;
             a.e_hi = e_hi;
             a.j = j;
-            a.keys = ws->f_keys.as<int32_t>();
-            a.vals = ws->f_vals.as<unsigned long long>();
+            a.tab = ws->f_keys.as<FrontierSlot>();
             a.rbase = r0;
             a.acc = ws->f_acc.as<unsigned long long>();
             a.n = n;
@@ -1265,13 +1263,13 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
             ++launches;
             if (Tc > 0) {  // count the pass's occupied slots, grow the next list to hold them, write them
                 const int64_t nb = fr_compact_blocks(Tc);
-                launch_fr_count(a.keys, Tc, ws->f_bcnt.as<long long>(), st);
+                launch_fr_count(a.tab, Tc, ws->f_bcnt.as<long long>(), st);
                 launch_scan64(ws->f_bcnt.as<long long>(), nb, ws->r_part.as<long long>(), ws->f_bpre.as<long long>(), st);
                 PS_CUDA(cudaMemcpyAsync(h_ll, ws->f_bpre.as<long long>() + nb, sizeof(long long), cudaMemcpyDeviceToHost, st));
                 PS_CUDA(cudaStreamSynchronize(st));
                 const long long need = std::max<long long>(1, out_n + h_ll[0]);
                 PS_ALLOC(grow_list(nx, need, out_n, st));
-                launch_fr_write(a.keys, a.vals, Tc, PR.roff, cuts[c], cuts[c + 1], r0, ws->f_bpre.as<long long>(),
+                launch_fr_write(a.tab, Tc, PR.roff, cuts[c], cuts[c + 1], r0, ws->f_bpre.as<long long>(),
                                 list_of(nx), out_n, need, st);
                 launches += 5;
                 out_n += h_ll[0];
@@ -1294,7 +1292,7 @@ static probesim_status run_batch_frontier(probesim_graph *g, Workspace *ws, cons
     const int32_t *counts = nullptr;
     if (switched > 0) {
         // the deterministic rounds' tables and lists are done with: their memory goes to Alg. 3's hash sets
-        for (DevBuf *b : {&ws->f_keys, &ws->f_vals, &ws->f_lp[0], &ws->f_lp[1], &ws->f_lx[0], &ws->f_lx[1],
+        for (DevBuf *b : {&ws->f_keys, &ws->f_lp[0], &ws->f_lp[1], &ws->f_lx[0], &ws->f_lx[1],
                           &ws->f_lv[0], &ws->f_lv[1], &ws->f_wp, &ws->f_sp, &ws->f_sx, &ws->f_sv})
             b->release();
         PS_TRY(rand_instances(g, ws, qb, B, P.W, max_len, t.walk_slot, t_sw, launches, st, too_big));
