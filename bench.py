@@ -72,8 +72,8 @@ def parse():
     ap.add_argument("--serve23-rates", default="2,4,6,8",
                     help="arrival rates of the serving leg on R-MAT 2^23 (empty = off)")
     ap.add_argument("--serve23-seconds", type=float, default=5.0)
-    ap.add_argument("--billion-batches", type=int, default=2,
-                    help="calls of 64 top-50 queries on R-MAT 2^25 with 10^9 edges (0 = off)")
+    ap.add_argument("--billion-batches", type=int, default=16,
+                    help="calls of 64 top-50 queries on R-MAT 2^25 with 10^9 edges (0 = off; 16 = 1,024 queries)")
     ap.add_argument("--billion-edges", type=float, default=1e9, help="edges of that graph")
     ap.add_argument("--accuracy-queries", type=int, default=5, help="queries of the pooling accuracy leg (0 = off)")
     ap.add_argument("--profile-case", choices=["frontier", "billion"], default=None,
