@@ -200,18 +200,19 @@ probesim_status probesim_set_memory_budget(probesim_graph *g, double bytes);
 /* Autotuner of the PROBE level kernel's launch shape on this graph.  It times the pull over the graph's own
  * in-lists for tile widths {1,2,4,8,16,32} columns and {2,4,8,16} blocks per SM (a constant-filled 64-column
  * score matrix, CUDA events, three runs after a warm-up), keeps the fastest shape per width and, for the
- * 32-column tiles of wide matrices, whichever of 32-column tiles, 16-column halves and 32-column tiles taken two
- * per pass (one read of the in-lists for both) takes less time.
+ * 32-column tiles of wide matrices, whichever of 32-column tiles, 16-column halves, 32-column tiles taken two
+ * per pass (one read of the in-lists for both) and 32-column tiles gathered by the TMA takes less time.
  * Later queries on the graph use the choice.  Takes about a second; results do not depend on it (only the
  * summation order). */
 probesim_status probesim_autotune(probesim_graph *g, void *stream);
-/* The current choice: *wide_tile in {16, 32, 64} (64: 32-column tiles two per pass); blocks_per_sm[6] for tile
- * widths 1, 2, 4, 8, 16, 32. */
+/* The current choice: *wide_tile in {16, 32, 64, 96} (see probesim_set_tuning); blocks_per_sm[6] for tile widths
+ * 1, 2, 4, 8, 16, 32. */
 probesim_status probesim_get_tuning(const probesim_graph *g, int32_t *wide_tile, int32_t *blocks_per_sm);
-/* Sets the launch shape by hand: wide_tile in {16, 32, 64}; blocks_per_sm (may be null: keep the current ones)
- * holds 7 entries in [1, 32], for tile widths 1, 2, 4, 8, 16, 32 and for the 32-column pairs.  Set it while no
- * call runs on the graph (the level loop reads the shape without a lock).  Results do not depend on it beyond
- * rounding: every tile shape adds a piece's in-neighbours in the same order. */
+/* Sets the launch shape by hand: wide_tile in {16, 32, 64, 96} (64: 32-column tiles two per pass; 96: 32-column
+ * tiles whose rows the Tensor Memory Accelerator gathers into shared memory, E_UNSUPPORTED without a tensor-map
+ * encoder in the driver); blocks_per_sm (may be null: keep the current ones) holds 8 entries in [1, 32], for tile
+ * widths 1, 2, 4, 8, 16, 32, the pairs and the TMA launch (at most 3 fit).  Set it while no call runs on the graph
+ * (the level loop reads the shape without a lock).  Results do not depend on it beyond rounding. */
 probesim_status probesim_set_tuning(probesim_graph *g, int32_t wide_tile, const int32_t *blocks_per_sm);
 probesim_status probesim_get_stats(const probesim_graph *g, probesim_stats *out);
 

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libprobesim.so")
-SOURCES = ["probesim.cu", "walk_trie.cu", "probe_level.cu", "pull.cu", "rand_probe.cu", "topk.cu", "topk_noalloc.cu", "server.cu", "graph_update.cu", "frontier.cu", "pair_mc.cu", "graph_build.cu"]
+SOURCES = ["probesim.cu", "walk_trie.cu", "probe_level.cu", "pull.cu", "rand_probe.cu", "topk.cu", "topk_noalloc.cu", "server.cu", "graph_update.cu", "frontier.cu", "pair_mc.cu", "graph_build.cu", "pull_tma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

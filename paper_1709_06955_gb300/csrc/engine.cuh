@@ -125,6 +125,7 @@ struct Workspace {
     DevBuf f_wslot, f_tsw, f_slot, f_misc, f_anc, f_deg, f_state, f_rsize, f_roff, f_dsize, f_doff, f_acc, f_tab, f_wp,
         f_lp[2], f_lx[2], f_lv[2], f_sp, f_sx, f_sv, f_cuts, f_keys, f_bcnt, f_bpre;
     DevBuf pm_in, pm_meets;  // pairwise Monte Carlo: pairs and keys, meet counts
+    DevBuf pull_err;         // set by the TMA pull when a stage's wait gives up
     bool f_table_clean = false;  // f_keys (the level table) holds only empty slots (every pass's compaction empties
                                  // its slots)
     PinnedBuf pin_q;  // query arrays of one batch
@@ -156,7 +157,7 @@ struct Workspace {
                           &tk_cid, &tk_cval, &tk_ids, &tk_vals, &tk_qk, &f_wslot, &f_tsw, &f_slot, &f_misc, &f_anc,
                           &f_deg, &f_state, &f_rsize, &f_roff, &f_dsize, &f_doff, &f_acc, &f_tab, &f_wp, &f_lp[0],
                           &f_lp[1], &f_lx[0], &f_lx[1], &f_lv[0], &f_lv[1], &f_sp, &f_sx, &f_sv, &f_cuts, &f_keys,
-                          &f_bcnt, &f_bpre, &pm_in, &pm_meets};
+                          &f_bcnt, &f_bpre, &pm_in, &pm_meets, &pull_err};
         for (DevBuf *b : bufs) b->release();
         f_table_clean = false;
         pin_q.release();
@@ -196,8 +197,8 @@ struct probesim_graph {
     std::atomic<size_t> budget{0};  // device memory one call's working buffers may take (set while calls run)
     size_t budget0 = 0;  // the default: 60% of device memory at creation
     // pull launch shape chosen by probesim_autotune (defaults until then)
-    int32_t tune_wide = 32;       // full tiles: 16, 32, or kPullPairs (32-column tiles two per pass)
-    int32_t tune_bps[65] = {0};   // blocks per SM per tile width, kPullPairs for the pairs (0 = default 8)
+    int32_t tune_wide = 32;       // full tiles: 16, 32, kPullPairs (32-column tiles two per pass) or kPullTma
+    int32_t tune_bps[128] = {0};  // blocks per SM per tile width, kPullPairs / kPullTma for those (0 = default)
     int32_t tuned = 0;
 };
 

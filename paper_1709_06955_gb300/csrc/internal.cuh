@@ -195,6 +195,15 @@ constexpr int32_t kPullPairs = 64;
 void launch_pull(const DeviceGraph &g, const float *D, int32_t dpitch, int64_t dts, int32_t dsub, float *MD,
                  int32_t pitch, int64_t mts, int32_t msub, int32_t ntiles, int32_t tile, int32_t blocks_per_sm,
                  const uint32_t *zmask, cudaStream_t s);
+// The pull over ntiles full 32-column tiles with TMA row gathers (pull_tma.cu); D's tiles as for launch_pull, plus
+// dcols = the columns of one row of D's layout (its pitch, or a group's width).  *err is set when a stage's wait
+// gives up.  Not available (cudaErrorNotSupported) when the driver gives no tensor-map encoder.
+constexpr int32_t kTmaMaxGroups = 8;   // groups of D one launch addresses (one tensor map each)
+constexpr int32_t kPullTma = 96;       // the tuner's name for this launch shape
+bool pull_tma_available();
+cudaError_t launch_pull_tma(const DeviceGraph &g, const float *D, int32_t dpitch, int32_t dcols, int64_t dts,
+                            int32_t dsub, float *MD, int32_t pitch, int64_t mts, int32_t msub, int32_t ntiles,
+                            int32_t blocks_per_sm, const uint32_t *zmask, int32_t *err, cudaStream_t s);
 void launch_gamma(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, TrieTable t, const float *inv_nr,
                   const float *MD, ColLayout L, cudaStream_t s);
 // out[q][v] = estimate + shift for v != u, out[q][u] = 1

@@ -688,9 +688,16 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     PS_CUDA(ws->md_b.ensure((size_t)max_floats * sizeof(float)));
     float *A = ws->md_a.as<float>(), *Bm = ws->md_b.as<float>();
     const int32_t *node_list = ws->node_list.as<int32_t>();
-    // the full tiles' launch: 32-column tiles, their 16-column halves, or 32-column tiles two per pass
-    const int32_t wide = g->tune_wide == 16 || g->tune_wide == kPullPairs ? g->tune_wide : 32;
-    const int32_t tw = wide == kPullPairs ? 32 : wide;
+    // the full tiles' launch: 32-column tiles, their 16-column halves, 32-column tiles two per pass, or 32-column
+    // tiles gathered by the TMA
+    const int32_t wide = g->tune_wide == 16 || g->tune_wide == kPullPairs || g->tune_wide == kPullTma ? g->tune_wide : 32;
+    const int32_t tw = wide == 16 ? 16 : 32;
+    int32_t *d_pull_err = nullptr;
+    if (wide == kPullTma) {
+        PS_CUDA(ws->pull_err.ensure(sizeof(int32_t)));
+        d_pull_err = ws->pull_err.as<int32_t>();
+        PS_CUDA(cudaMemsetAsync(d_pull_err, 0, sizeof(int32_t), st));
+    }
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> marks;
     // Without profiling, the push block and the tail tile of a depth run on a second stream beside the
     // accumulate and the full-tile pull: they write other columns of A than the full tiles do.  With
@@ -759,7 +766,12 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
                             tail[d], g->tune_bps[tail[d]], zmask_at(d) ? zmask_at(d) + nfull[d] : nullptr, ss);
                 ++launches;
             }
-            if (nfull[d] > 0) {  // 32-column tiles (or their 16-column halves, or pairs of them)
+            if (nfull[d] > 0 && wide == kPullTma) {  // 32-column tiles, rows gathered by the TMA
+                PS_CUDA(launch_pull_tma(dg, Bm, Lb.rpitch(0), Lb.K > 0 ? kGroup : Lb.R, Lb.tile_stride(), Lb.tile_sub(32),
+                                        A, La.rpitch(0), La.tile_stride(), La.tile_sub(32), nfull[d],
+                                        g->tune_bps[kPullTma], zmask_at(d), d_pull_err, st));
+                ++launches;
+            } else if (nfull[d] > 0) {  // 32-column tiles (or their 16-column halves, or pairs of them)
                 const int32_t nt = nfull[d] * (32 / tw);
                 launch_pull(dg, Bm, Lb.rpitch(0), Lb.tile_stride(), Lb.tile_sub(tw), A, La.rpitch(0), La.tile_stride(),
                             La.tile_sub(tw), nt, wide, g->tune_bps[wide], zmask_at(d), st);
@@ -799,7 +811,10 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
     ph.end();
     ++launches;
     PS_CUDA(cudaGetLastError());
+    int32_t pull_err = 0;
+    if (d_pull_err) PS_CUDA(cudaMemcpyAsync(&pull_err, d_pull_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
+    if (pull_err) return fail(PROBESIM_E_TIMEOUT, "a TMA row gather of the pull did not complete in time");
     ph.collect(ws->stats);
     for (auto &mk : marks) {
         float ms = 0.f;
@@ -1883,8 +1898,8 @@ probesim_status probesim_autotune(probesim_graph *g, void *stream) {
     }
     // wide tiles: two 32-column tiles of a node-major [n][64] matrix, as 32-column tiles, 16-column halves, or one
     // pass over both
-    double per_col[kPullPairs + 1] = {0};
-    int32_t wide_bps[kPullPairs + 1] = {0};
+    double per_col[kPullTma + 1] = {0};
+    int32_t wide_bps[kPullTma + 1] = {0};
     for (int32_t T : {16, 32, kPullPairs}) {
         float best = 1e30f;
         for (int32_t bps : bpss) {
@@ -1895,10 +1910,26 @@ probesim_status probesim_autotune(probesim_graph *g, void *stream) {
         }
         per_col[T] = best / 3.0 / 64.0;
     }
+    if (pull_tma_available()) {  // the TMA gathers (one block of 192 KB shared memory per SM)
+        PS_CUDA(ws->pull_err.ensure(sizeof(int32_t)));
+        PS_CUDA(cudaMemsetAsync(ws->pull_err.p, 0, sizeof(int32_t), st));
+        cudaError_t le = cudaSuccess;
+        const float best = time_pull([&] {
+            le = launch_pull_tma(dg, Da, P, P, 0, 1 << 30, Mb, P, 0, 1 << 30, 2, 1, nullptr, ws->pull_err.as<int32_t>(),
+                                 st);
+        });
+        PS_CUDA(le);
+        wide_bps[kPullTma] = 1;
+        int32_t herr = 0;
+        PS_CUDA(cudaMemcpyAsync(&herr, ws->pull_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        if (herr) return fail(PROBESIM_E_TIMEOUT, "a TMA row gather of the pull did not complete in time");
+        per_col[kPullTma] = best / 3.0 / 64.0;
+    }
     PS_CUDA(cudaGetLastError());
     int32_t pick = 32;
-    for (int32_t T : {16, kPullPairs})
-        if (per_col[T] < per_col[pick]) pick = T;
+    for (int32_t T : {16, kPullPairs, kPullTma})
+        if (per_col[T] > 0 && per_col[T] < per_col[pick]) pick = T;
     g->tune_bps[32] = wide_bps[32];
     g->tune_bps[pick] = wide_bps[pick];
     g->tune_wide = pick;
@@ -1909,10 +1940,12 @@ probesim_status probesim_autotune(probesim_graph *g, void *stream) {
 
 probesim_status probesim_set_tuning(probesim_graph *g, int32_t wide_tile, const int32_t *blocks_per_sm) {
     if (!g) return fail(PROBESIM_E_INVALID, "graph is null");
-    if (wide_tile != 16 && wide_tile != 32 && wide_tile != kPullPairs)
-        return fail(PROBESIM_E_INVALID, "wide_tile must be 16, 32 or 64");
+    if (wide_tile != 16 && wide_tile != 32 && wide_tile != kPullPairs && wide_tile != kPullTma)
+        return fail(PROBESIM_E_INVALID, "wide_tile must be 16, 32, 64 or 96");
+    if (wide_tile == kPullTma && !pull_tma_available())
+        return fail(PROBESIM_E_UNSUPPORTED, "no tensor-map encoder in this driver");
     if (blocks_per_sm)
-        for (int i = 0; i < 7; ++i)
+        for (int i = 0; i < 8; ++i)
             if (blocks_per_sm[i] < 1 || blocks_per_sm[i] > 32)
                 return fail(PROBESIM_E_INVALID, "blocks_per_sm must lie in [1, 32]");
     std::lock_guard<std::mutex> lk(g->mu);
@@ -1920,6 +1953,7 @@ probesim_status probesim_set_tuning(probesim_graph *g, int32_t wide_tile, const 
     if (blocks_per_sm) {
         for (int i = 0; i < 6; ++i) g->tune_bps[1 << i] = blocks_per_sm[i];
         g->tune_bps[kPullPairs] = blocks_per_sm[6];
+        g->tune_bps[kPullTma] = blocks_per_sm[7];
     }
     return PROBESIM_OK;
 }

@@ -340,14 +340,15 @@ class Graph:
         return {"wide_tile": wide.value, "blocks_per_sm": {1 << i: bps[i] for i in range(6)}}
 
     def set_tuning(self, wide_tile, blocks_per_sm=None):
-        """Sets the pull's launch shape by hand (probesim_set_tuning): wide_tile 16, 32 or 64 (32-column tiles two
-        per pass); blocks_per_sm, if given, 7 values for tile widths 1..32 and the pairs."""
+        """Sets the pull's launch shape by hand (probesim_set_tuning): wide_tile 16, 32, 64 (32-column tiles two per
+        pass) or 96 (32-column tiles gathered by the TMA); blocks_per_sm, if given, 8 values for tile widths 1..32,
+        the pairs and the TMA launch."""
         arr = None
         if blocks_per_sm is not None:
             vals = [int(b) for b in blocks_per_sm]
-            if len(vals) != 7:
-                raise ValueError("blocks_per_sm needs 7 values")
-            arr = (C.c_int32 * 7)(*vals)
+            if len(vals) != 8:
+                raise ValueError("blocks_per_sm needs 8 values")
+            arr = (C.c_int32 * 8)(*vals)
         _check(load().probesim_set_tuning(self._h, int(wide_tile), arr))
 
     def set_memory_budget(self, nbytes):

@@ -282,9 +282,10 @@ def test_autotune_keeps_results(cfg1):
 
 
 def test_every_pull_shape_gives_the_same_scores():
-    """Full tiles as 16-column halves, 32-column tiles, or 32-column tiles two per pass (with an odd tile count at
-    some depths, so a pass holds one tile): each adds a piece's in-neighbours in the same order, so the scores agree
-    to rounding (rows cut into several pieces add the pieces atomically, in any order), and within 1e-5 of the
+    """Full tiles as 16-column halves, 32-column tiles, 32-column tiles two per pass (with an odd tile count at
+    some depths, so a pass holds one tile), or 32-column tiles gathered by the TMA: the first three add a piece's
+    in-neighbours in the same order and the TMA pull in four interleaved partial sums, so the scores agree to
+    rounding (rows cut into several pieces also add their pieces atomically, in any order), and within 1e-5 of the
     oracle.  R-MAT 2^12, eps 0.1: the widest depths have hundreds of columns."""
     from paper_1709_06955_gb300 import probesim
     n, s, d = synth.rmat(12, 16 << 12, seed=12)
@@ -292,13 +293,15 @@ def test_every_pull_shape_gives_the_same_scores():
     qs = synth.queries(n, d, 2, seed=13)
     Q = _q(qs, eps=0.1, query_ids=[21, 22])
     outs = {}
-    for wide in (32, 16, 64):
-        G.set_tuning(wide, [8, 8, 8, 4, 4, 4, 3])
+    for wide in (32, 16, 64, 96):
+        G.set_tuning(wide, [8, 8, 8, 4, 4, 4, 3, 2])
         assert G.tuning()["wide_tile"] == wide
         outs[wide] = G.single_source(Q)
-    assert np.max(np.abs(outs[32] - outs[16])) <= 1e-6 and np.max(np.abs(outs[32] - outs[64])) <= 1e-6
+    for wide in (16, 64, 96):
+        assert np.max(np.abs(outs[32] - outs[wide])) <= 1e-6
     for t, u in enumerate(qs):
-        ref, _ = O.single_source(int(u), eps=0.1, seed=3, qid=21 + t)
-        assert np.max(np.abs(outs[64][t] - ref)) <= TOL
+        for wide in (64, 96):
+            ref, _ = O.single_source(int(u), eps=0.1, seed=3, qid=21 + t)
+            assert np.max(np.abs(outs[wide][t] - ref)) <= TOL
     with pytest.raises(probesim.ProbeSimError):
         G.set_tuning(48)
