@@ -76,7 +76,7 @@ def parse():
                     help="calls of 64 top-50 queries on R-MAT 2^25 with 10^9 edges (0 = off; 16 = 1,024 queries)")
     ap.add_argument("--billion-edges", type=float, default=1e9, help="edges of that graph")
     ap.add_argument("--accuracy-queries", type=int, default=5, help="queries of the pooling accuracy leg (0 = off)")
-    ap.add_argument("--profile-case", choices=["frontier", "billion"], default=None,
+    ap.add_argument("--profile-case", choices=["frontier", "billion", "pull"], default=None,
                     help="run one fixed case for an ncu capture and exit (see profile_case)")
     return ap.parse_args()
 
@@ -667,12 +667,23 @@ def profile_case(args):
 
     frontier: R-MAT 2^20 drawn on the GPU, switch mode c0 = 0.01, two calls of four queries at eps = 0.1.
     billion:  R-MAT 2^25 with 10^9 edges drawn and built on the GPU, switch mode c0 = 0.01, one call of 64 top-50
-              queries at eps = 0.1 (the billion-edge leg's call)."""
+              queries at eps = 0.1 (the billion-edge leg's call).
+    pull:     R-MAT 2^18 (the host generator, m = 2^22), deterministic PROBE with the full tiles pinned to single
+              32-column tiles at 8 blocks per SM (no tuner, so a capture does not depend on timings taken under a
+              profiler), two queries at eps = 0.1 one per call."""
     import numpy as np
     import torch
     from paper_1709_06955_gb300 import build, probesim, synth
     build.build()
-    if args.profile_case == "billion":
+    if args.profile_case == "pull":
+        n, s, d = synth.config_graph("rmat-18")
+        qs = synth.queries(n, d, 2, seed=2)
+        G = probesim.Graph(n, s, d)
+        G.set_tuning(32, [16, 16, 16, 16, 16, 8, 3, 1])
+        out = torch.zeros((1, n), dtype=torch.float32, device="cuda")
+        for i in range(2):
+            G.single_source(probesim.make_queries(qs[i:i + 1], eps=EPS, query_ids=[i]), out=out)
+    elif args.profile_case == "billion":
         n, s, d = synth.rmat_device(25, int(args.billion_edges), seed=1)
         torch.cuda.empty_cache()
         qs = synth.queries(n, d, 64, seed=2)
