@@ -245,6 +245,18 @@ __global__ void k_build_out_col(const uint64_t *__restrict__ okeys, int64_t mu, 
         out_col[e] = (int32_t)(okeys[e] & smask);
 }
 
+__global__ void k_active_rows(const int64_t *__restrict__ out_off, int32_t n, int32_t *res) {
+    int32_t best = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (out_off[v + 1] > out_off[v]) best = (int32_t)v + 1;
+    for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(res, best);
+}
+
+void launch_active_rows(const int64_t *out_off, int32_t n, int32_t *res, cudaStream_t s) {
+    k_active_rows<<<build_blocks(n, 256), 256, 0, s>>>(out_off, n, res);
+}
+
 void launch_build_keys(const int32_t *src, const int32_t *dst, int64_t m, int32_t n, int bs, uint64_t *keys,
                        int32_t *bad, cudaStream_t s) {
     if (m > 0) k_build_keys<<<build_blocks(m, 256), 256, 0, s>>>(src, dst, m, n, bs, keys, bad);

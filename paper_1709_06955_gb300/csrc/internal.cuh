@@ -63,6 +63,8 @@ struct DeviceGraph {
     int32_t *piece_len = nullptr;  // length | (split ? 1 << 31 : 0)
     int32_t n_split = 0;           // vertices cut into more than one piece
     int32_t *split_v = nullptr;
+    int32_t n_active = 0;          // every node with out-edges has an internal id below n_active (all of them
+                                   // come first at creation; update batches may leave gaps)
     int32_t *ext2int = nullptr;    // caller's node id -> internal id (descending out-degree order)
     int32_t *int2ext = nullptr;    // internal id -> caller's node id
 };
@@ -369,6 +371,8 @@ void launch_build_in_col(int32_t n, const int32_t *int2ext, const long long *ext
                          const uint64_t *ukeys, uint32_t smask, const int32_t *ext2int, int bs, int32_t *in_col,
                          uint64_t *okeys, cudaStream_t s);
 void launch_build_out_col(const uint64_t *okeys, int64_t mu, uint32_t smask, int32_t *out_col, cudaStream_t s);
+// *res = 1 + the largest v with out-edges (0 if none); *res must be 0 before the launch
+void launch_active_rows(const int64_t *out_off, int32_t n, int32_t *res, cudaStream_t s);
 
 // sets the message probesim_last_error() returns on the calling thread
 void set_last_error(const char *msg);

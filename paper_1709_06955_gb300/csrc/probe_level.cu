@@ -124,6 +124,8 @@ void launch_push_h2(const DeviceGraph &g, const int32_t *nodes, int32_t cnt, Tri
 // over the parts; the later parts of groups with more than four sources add atomically after the row's first
 // parts are done.  Heirs and push heirs leave few parts per depth, so the kernel touches a few sectors of
 // each row in place (measured faster than streaming whole rows through shared memory at every batch width).
+// Only rows below n_active are accumulated: a row of a node without out-edges is never read once accumulated (the
+// pull and the gamma gather in-neighbours' rows), and the renumbering puts those nodes last.
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ float acc_part_sum(const float *B, const ColLayout &L, int64_t v, int4 sc) {
     float sum = 0.f;

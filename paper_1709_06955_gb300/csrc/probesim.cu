@@ -191,6 +191,10 @@ static probesim_status build_graph(probesim_graph *g, int32_t n, const int32_t *
                       sv->piece_v.as<int32_t>(), sv->piece_beg.as<int64_t>(), sv->piece_len.as<int32_t>(), st);
     std::vector<unsigned long long> hh(kPiece + 2);
     long long ends[2] = {0, 0};
+    int32_t n_active = 0;
+    PS_CUDA(cudaMemsetAsync(t.flag.p, 0, sizeof(int32_t), st));
+    launch_active_rows(sv->out_off.as<int64_t>(), n, t.flag.as<int32_t>(), st);
+    PS_CUDA(cudaMemcpyAsync(&n_active, t.flag.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(hh.data(), hist, sizeof(unsigned long long) * (kPiece + 1), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(hh.data() + kPiece + 1, nsplit, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(&ends[0], sv->in_off.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st));
@@ -215,6 +219,7 @@ static probesim_status build_graph(probesim_graph *g, int32_t n, const int32_t *
     d.piece_beg = sv->piece_beg.as<int64_t>();
     d.piece_len = sv->piece_len.as<int32_t>();
     d.n_split = (int32_t)hh[kPiece + 1];
+    d.n_active = n_active;
     d.split_v = sv->split_v.as<int32_t>();
     d.ext2int = g->ext2int.as<int32_t>();
     d.int2ext = g->int2ext.as<int32_t>();
@@ -730,7 +735,7 @@ static probesim_status run_batch(probesim_graph *g, Workspace *ws, const probesi
             ph.begin(2);  // D of this depth's dense nodes, in place in B (the MD of depth d+1)
             const int32_t np1 = p1_at[d + 1] - p1_at[d], np2 = p2_at[d + 1] - p2_at[d];
             if (np1 > 0)
-                launch_accumulate(n, Bm, Lb, d_sched + o_p1dst + p1_at[d],
+                launch_accumulate(dg.n_active, Bm, Lb, d_sched + o_p1dst + p1_at[d],
                                   reinterpret_cast<const int4 *>(d_sched + o_p1src) + p1_at[d], np1,
                                   d_sched + o_p2dst + p2_at[d],
                                   reinterpret_cast<const int4 *>(d_sched + o_p2src) + p2_at[d], np2, st);
@@ -1670,9 +1675,15 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
                        *nsplit = cursor + (kPiece + 1);
     launch_upd_pieces(n, n_in_off.as<long long>(), hist, cursor, n_split.as<int32_t>(), nsplit, n_pv.as<int32_t>(),
                       n_pb.as<int64_t>(), n_pl.as<int32_t>(), st);
+    // the rows with out-edges after the batch (the last slot of the histogram buffer is free)
+    int32_t *d_active = reinterpret_cast<int32_t *>(nsplit + 1);
+    PS_CUDA(cudaMemsetAsync(d_active, 0, sizeof(int32_t), st));
+    launch_active_rows(n_out_off.as<int64_t>(), n, d_active, st);
     std::vector<unsigned long long> hh(kPiece + 2);
+    int32_t n_active = 0;
     PS_CUDA(cudaMemcpyAsync(hh.data(), hist, sizeof(unsigned long long) * (kPiece + 1), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(hh.data() + kPiece + 1, nsplit, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(&n_active, d_active, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaGetLastError());
     PS_CUDA(cudaStreamSynchronize(st));
     int64_t npieces = 0;
@@ -1692,6 +1703,7 @@ probesim_status ps::apply_updates(probesim_graph *g, const int32_t *src, const i
     ng.piece_len = nv->piece_len.as<int32_t>();
     ng.n_split = (int32_t)hh[kPiece + 1];
     ng.split_v = nv->split_v.as<int32_t>();
+    ng.n_active = n_active;
     nv->epoch = old->epoch + 1;
     g->publish(nv);
     if (applied) *applied = hm[2];

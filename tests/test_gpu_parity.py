@@ -249,6 +249,28 @@ def test_updates_on_a_hub_row():
             assert lens[k] == w.size and np.array_equal(nodes[k, :w.size], w)
 
 
+def test_updates_give_out_edges_to_nodes_without_any():
+    """Nodes without out-edges come last in the internal order, and the level loop skips their rows when it
+    accumulates (nothing gathers them).  An update batch that gives forty of them out-edges into the most popular
+    targets must bring their rows back: estimates and walks of queries at those targets match the oracle."""
+    n = 2000
+    s, d = synth.chung_lu(n, 12000, seed=8)
+    quiet = np.nonzero(np.bincount(s, minlength=n) == 0)[0][:40]
+    assert quiet.size == 40
+    targets = np.argsort(-np.bincount(d, minlength=n), kind="stable")[:5]
+    add_s = np.repeat(quiet, targets.size).astype(np.int32)
+    add_d = np.tile(targets, quiet.size).astype(np.int32)
+    G = gpu_graph(n, s, d)
+    G.insert_edges(add_s, add_d)
+    cur_s, cur_d = dedup(n, np.concatenate([s, add_s]), np.concatenate([d, add_d]))
+    assert G.info()[1] == cur_s.size
+    O = oracle_graph(n, cur_s, cur_d)
+    for t, u in enumerate(targets[:3]):
+        out = G.single_source(_q([int(u)], eps=0.15, query_ids=[t]))[0]
+        ref, _ = O.single_source(int(u), eps=0.15, seed=3, qid=t)
+        assert np.max(np.abs(out - ref)) <= TOL
+
+
 def test_errors(cfg1):
     from paper_1709_06955_gb300 import probesim
     n, s, d, G, O = cfg1
