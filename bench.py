@@ -69,8 +69,9 @@ def parse():
     ap.add_argument("--switch-c0", type=float, default=0.01, help="c0 of the switch legs (Sec. 4.4)")
     ap.add_argument("--mixed-batch", type=int, default=256,
                     help="queries of the mixed-eps top-50 call on R-MAT 2^22 (0 = off)")
-    ap.add_argument("--serve23-rates", default="2,4,6,8",
-                    help="arrival rates of the serving leg on R-MAT 2^23 (empty = off)")
+    ap.add_argument("--serve23-rates", default="2,4,6,8,10,20",
+                    help="arrival rates of the serving leg on R-MAT 2^23 (empty = off); capacity is near 9 q/s, so "
+                         "10 and 20 (the low end of the configuration's sweep) show the queue building")
     ap.add_argument("--serve23-seconds", type=float, default=5.0)
     ap.add_argument("--billion-batches", type=int, default=16,
                     help="calls of 64 top-50 queries on R-MAT 2^25 with 10^9 edges (0 = off; 16 = 1,024 queries)")
