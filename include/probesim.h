@@ -102,8 +102,11 @@ typedef struct {
 probesim_status probesim_split_error(double eps_a, double c, int32_t shift, probesim_error_split *out);
 
 /* Builds the device graph store from m directed edges src[e] -> dst[e] (Sec. 2.1: a directed simple
- * graph).  Self-loops and duplicate edges are dropped (a simple graph has neither) and the number kept
- * is reported by probesim_graph_info.  n >= 1, 0 <= m < 2^31.  On success *out owns the graph. */
+ * graph).  src and dst may be host or device arrays (host arrays are copied to the device first); the build runs
+ * on the device (radix sorts of the edge keys; it takes about 24 bytes of device memory per edge beyond the
+ * store).  Self-loops and duplicate edges are dropped (a simple graph has neither) and the number kept is reported
+ * by probesim_graph_info.  An id outside [0, n) gives E_RANGE and no graph.  n >= 1, 0 <= m < 2^31.  On success
+ * *out owns the graph; the call synchronises `stream`. */
 probesim_status probesim_graph_create(int32_t n, const int32_t *src, const int32_t *dst, int64_t m,
                                       const probesim_config *cfg, void *stream, probesim_graph **out);
 
