@@ -115,22 +115,26 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def recorded_traffic():
-    """DRAM bytes / algorithmic bytes of the PROBE level kernel from the committed ncu summary, valid only
-    while the kernel source is unchanged since the capture (checked by its hash)."""
+def recorded_pull_counters():
+    """From the committed ncu summary of the PROBE level kernel, valid only while the kernel source is unchanged
+    since the captures (checked by its hash): the full-size DRAM / algorithmic byte ratio, and the share of its
+    L1 data pipe's wavefront peak it used (the unit that bounds it).  (None, None) when absent or stale."""
     import hashlib
     src = os.path.join(ROOT, "paper_1709_06955_gb300", "csrc", "pull.cu")
     summ = os.path.join(ROOT, "profiles", "k_pull_traffic.txt")
+    ratio = pipe = None
     try:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         for line in open(summ):
-            if line.startswith("ratio "):
-                _, ratio, src_hash = line.split()[:3]
-                if src_hash == h:
-                    return float(ratio)
+            parts = line.split()
+            if len(parts) >= 3 and parts[2] == h:
+                if parts[0] == "ratio":
+                    ratio = float(parts[1])
+                elif parts[0] == "l1pipe":
+                    pipe = float(parts[1])
     except Exception:  # noqa: BLE001
         pass
-    return None
+    return ratio, pipe
 
 
 class ClockSampler:
@@ -615,7 +619,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak_hbm()
     # the pull's roofline, from the profiled pass (CUDA events around every pull launch)
     achieved = prof["probe_bytes"] / (prof["probe_ms"] / 1e3) / 1e9 if prof["probe_ms"] > 0 else None
-    ratio = recorded_traffic()
+    ratio, l1pipe = recorded_pull_counters()
     per_launch = prof["probe_bytes"] / max(1, prof["probe_launches"])
     roof = {"kernel": "k_pull (PROBE level pull, pull.cu)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_kind": peak_kind + " hbm_gbs (copy)", "unit": "GB/s",
@@ -624,7 +628,9 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": per_launch, "launches": prof["probe_launches"],
             "profiled_queries": np_,
             "kernel_ms_share_of_step": prof["probe_ms"] / prof["step_ms"] if prof["step_ms"] else None,
-            "l2_gather_GBps": 4.0 * prof["edge_gathers"] / (prof["probe_ms"] / 1e3) / 1e9 if prof["probe_ms"] else None}
+            "l2_gather_GBps": 4.0 * prof["edge_gathers"] / (prof["probe_ms"] / 1e3) / 1e9 if prof["probe_ms"] else None,
+            "binding_unit": {"unit": "L1 data-pipe wavefronts (ncu, profiles/k_pull_rmat18_one_query.md)",
+                             "frac": l1pipe}}
     lat_sorted = sorted(lat)
 
     def pct(p):
