@@ -181,7 +181,9 @@ __global__ void k_build_compact(const uint64_t *__restrict__ keys, int64_t m, ui
 }
 
 // ext_off[v] = first index of destination v's run in the sorted unique keys, v = 0..n (each v written once: by the
-// key that starts the first run at or after v, or by index mu for the rows after the last run)
+// key that starts the first run at or after v, or by index mu for the rows after the last run).  One pass over the
+// keys; the thread at a run boundary also fills the nodes without in-edges just before it, so a long stretch of
+// such nodes is written by one thread (on power-law inputs the stretches are short).
 __global__ void k_build_ext_off(const uint64_t *__restrict__ ukeys, int64_t mu, int32_t n, int bs,
                                 long long *__restrict__ ext_off) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= mu; i += (int64_t)gridDim.x * blockDim.x) {
